@@ -1,0 +1,274 @@
+#!/usr/bin/env python3
+"""RecSplit construction benchmark on one node.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one complete build (fingerprint, bucket sort, split and leaf
+searches with rotation fitting, Golomb-Rice / Elias-Fano packing) of the
+10,000,000-key workload with leaf size 16 and bucket size 2000, keys already
+resident in device memory.  Prints one JSON line (rank 0).  N > 1 runs one
+independent build per GPU (weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle on the host cores on a bounded bucket
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2212_09562_b300 import workloads as W  # noqa: E402
+
+METRIC = "MPHF build keys/s + seed trials/s vs IMAD peak (ℓ=16,b=2000), batched vs plain"
+WORKLOAD = "rot_l16"
+# Integer instructions that one key-hash evaluation needs at least on 32-bit
+# integer lanes: 64-bit add (2), three 64-bit xor-shifts (4 each), two
+# 64x64->64 multiplies (3 each), exact 64-bit mod m by a constant (3 wide
+# multiply-adds + 3 for the final 32-bit remainder), child counter update (3).
+OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
+SMS, SMSP_PER_SM, LANES, SM_MAX_MHZ = 148, 4, 32, 2032.0
+PEAK_INT_OPS = SMS * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6  # issue-slot bound, lane-ops/s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.file.flush()
+        self.file.seek(0)
+        rows = [l.strip().split(",") for l in self.file.read().splitlines() if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, keys, budget_s: float) -> dict:
+    """The oracle as it stands, on all host cores, on a bounded bucket sample."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    nb = (w.n + w.bucket - 1) // w.bucket
+    # size the sample from one bucket's single-thread time
+    probe = W.sample_buckets(nb, 1, w.seed + 99)
+    t0 = time.perf_counter()
+    O.build_sample(keys, w.leaf, w.bucket, w.rotation, probe, threads=1)
+    one = time.perf_counter() - t0
+    count = int(max(1, min(nb, round(budget_s * cores / max(one, 1e-3)))))
+    count = max(cores, count - count % cores) if count >= cores else count
+    sample = W.sample_buckets(nb, count, w.seed + 100)
+    t0 = time.perf_counter()
+    vals, counts, st = O.build_sample(keys, w.leaf, w.bucket, w.rotation, sample, threads=cores)
+    dt = time.perf_counter() - t0
+    hi, _ = O.fingerprint(keys)
+    b = (hi.astype(object) * nb >> 64).astype(np.int64)
+    sample_keys = int(np.isin(b, sample.astype(np.int64)).sum())
+    trials = sum(v[0] for v in st.values())
+    return {"value": sample_keys / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
+            "sample": f"{count} of {nb} buckets ({sample_keys} keys) of {w.name}, seeded",
+            "seconds": dt, "trials_per_s": trials / dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = W.WORKLOADS[args.workload]
+    keys = W.keys_for(w)
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_baseline(w, keys, 2.0)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(w, keys, args.cpu_seconds / max(1, args.steps))
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = statistics.mean(vals)
+    out = {"metric": METRIC, "value": v, "unit": "keys/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(secs),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "bucket": w.bucket,
+                      "rotation": w.rotation, "key_bytes": w.key_bytes, "sample": r["sample"]},
+           "cpu_baseline": {"value": v, "unit": "keys/s", "cores": r["cores"], "kind": "oracle",
+                            "sample": r["sample"]},
+           "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2212_09562_b300 import mphf as M
+    M.lib()
+    w = W.WORKLOADS[args.workload]
+    keys = W.random_keys(w.n, w.key_bytes, w.seed + rank) if rank else W.keys_for(w)
+    dkeys = torch.from_numpy(keys.view(np.int64) if keys.ndim == 1 else keys).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation).close()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, search_ms, evals, trials = [], [], 0, 0
+    launches0 = M.kernel_launches()
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (outside the step's events)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        g = M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        st = g.stats()
+        search_ms.append(st["ms"]["search"])
+        evals += sum(st[k][1] for k in ("leaf", "lower1", "lower2", "upper"))
+        trials += sum(st[k][0] for k in ("leaf", "lower1", "lower2", "upper"))
+        if i == args.steps - 1:
+            bad = g.verify(dkeys)
+            assert bad == 0, f"built function is not a bijection ({bad} bad keys)"
+        g.close()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    launches = M.kernel_launches() - launches0 - 3  # minus the final verify's query/mark/memset-free
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    keys_per_s = world * args.steps * w.n / (total_ms / 1000.0)
+
+    # end to end through the public host-buffer call: pinned keys in, packed function out
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = torch.from_numpy(keys.view(np.int64) if keys.ndim == 1 else keys).pin_memory()
+        host_view = pinned.numpy().view(np.uint64) if keys.ndim == 1 else pinned.numpy()
+        times, d2h = [], 0
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = M.MPHF.build_host(host_view, w.leaf, w.bucket, w.rotation)
+            blob = g.serialize()
+            times.append(time.perf_counter() - t0)
+            d2h = len(blob)
+            g.close()
+        e2e = {"value": world * w.n / statistics.mean(times), "unit": "keys/s",
+               "h2d_bytes_per_step": int(keys.nbytes), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        return
+    mean_search = statistics.mean(search_ms)
+    evals_per_build = evals / args.steps
+    ops = evals_per_build * OPS_PER_EVAL
+    achieved = ops / (mean_search / 1000.0)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_INT_OPS / 1e12,
+            "unit": "Tintops/s", "frac": achieved / PEAK_INT_OPS, "traffic": None,
+            "kernel": "k_search", "ops_per_eval": OPS_PER_EVAL,
+            "evals_per_launch": evals_per_build, "launch_ms": mean_search,
+            "peak_basis": "148 SMs x 4 SMSP x 32 lanes x 2032 MHz (integer issue slots)"}
+    out = {"metric": METRIC, "value": keys_per_s, "unit": "keys/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic",
+           "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "bucket": w.bucket,
+                      "rotation": w.rotation, "key_bytes": w.key_bytes,
+                      "l2": "flushed between steps (256 MB write)",
+                      "parallelism": f"{world} independent builds (one per GPU)"},
+           "trials_per_s": world * trials / (total_ms / 1000.0),
+           "evals_per_s": world * evals / (total_ms / 1000.0),
+           "search_ms": mean_search, "wall_s": wall,
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, keys, args.cpu_seconds)
+        out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * mphf.h -- C ABI of the B300 RecSplit construction library (libmphf.so).
+ *
+ * Builds a RecSplit minimal perfect hash function (MPHF) with rotation
+ * fitting on one CUDA device, after Bez, Kurpicz, Lehmann and Sanders,
+ * "High Performance Construction of RecSplit Based Minimal Perfect Hash
+ * Functions" (arXiv 2212.09562).  The problem (Section 1): given a set S of
+ * n distinct keys, build h with h bijective from S onto [0, n); outside S the
+ * value is arbitrary.
+ *
+ * Conventions for every entry point:
+ *   - Pointers prefixed d_ are device pointers, h_ are host pointers.
+ *   - Streams are cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Work is ordered on the given stream.  Functions that return
+ *     a device-side error code (build, verify) synchronise the stream
+ *     before returning; mphf_query does not.
+ *   - Keys are caller-owned, 8-byte aligned, and must stay valid until the
+ *     call returns.
+ *     A key is 8 bytes (one little-endian 64-bit word) or 16 bytes (two
+ *     words, the first is w0).  Keys must be distinct.
+ *   - Everything a build allocates belongs to the returned mphf_t and is
+ *     released by mphf_free.  Device memory comes from the allocator in the
+ *     build parameters, or from cudaMallocAsync on the stream.
+ *   - Every function returns MPHF_OK (0) or a negative error code below.  No
+ *     exception crosses the ABI and no device code traps: device errors are
+ *     reported through a status word that the host reads.
+ */
+#ifndef MPHF_H
+#define MPHF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPHF_OK 0
+#define MPHF_EINVAL (-1)         /* bad argument: leaf_size, bucket_size, key_bytes, n, NULL  */
+#define MPHF_ENOMEM (-2)         /* an allocation failed                                     */
+#define MPHF_ECUDA (-3)          /* a CUDA runtime call failed                               */
+#define MPHF_EDUPLICATE (-4)     /* two keys of one bucket share the fingerprint's lo word   */
+#define MPHF_ESEARCH_LIMIT (-5)  /* some node needs a value above max_value                  */
+#define MPHF_EBUSY (-6)          /* server full (no free slot or device memory)              */
+#define MPHF_EBUCKET (-7)        /* a bucket holds more than MPHF_MAX_BUCKET keys            */
+#define MPHF_ENOTIMPL (-8)       /* not supported by this build of the library               */
+#define MPHF_ETIMEOUT (-9)       /* a bounded device wait gave up                            */
+
+#define MPHF_MAX_BUCKET 4096u    /* largest bucket a build accepts (keys)                    */
+#define MPHF_MAX_LEAF 24u        /* leaf sizes 2..24                                          */
+#define MPHF_MAX_BUCKET_SIZE 3000u /* bucket_size parameter b in 1..3000                      */
+#define MPHF_DEFAULT_MAX_VALUE 0xFFFFFFFFFFull /* 2^40 - 1                                    */
+
+typedef struct mphf mphf_t;
+
+/* Device allocator hooks.  alloc returns NULL on failure. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} mphf_allocator;
+
+/* Build parameters.  Fields left 0 by mphf_default_params take defaults.
+ *   leaf_size        l, 2..24 (Section 2.2: leaves of l keys).
+ *   bucket_size      b, 1..3000; nb = ceil(n / b) buckets.
+ *   key_bytes        8 or 16.
+ *   rotation_fitting 1: leaves use rotation fitting (Section 3); 0: plain
+ *                    brute force (Section 2.2, "Bijections").
+ *   max_value        largest value any node may store; a node that needs
+ *                    more fails the build with MPHF_ESEARCH_LIMIT.
+ *   threads_per_block, blocks_per_sm
+ *                    launch shape of the search kernel; 0 = the tuned or
+ *                    default choice. */
+typedef struct {
+    uint32_t leaf_size;
+    uint32_t bucket_size;
+    uint32_t key_bytes;
+    uint32_t rotation_fitting;
+    uint64_t max_value;
+    const mphf_allocator *allocator;
+    uint32_t threads_per_block;
+    uint32_t blocks_per_sm;
+} mphf_build_params;
+
+/* Sizes and parameters of a built function. */
+typedef struct {
+    uint64_t n, nb;            /* keys, buckets                                    */
+    uint32_t leaf_size, bucket_size, key_bytes, rotation_fitting;
+    uint64_t n_nodes;          /* stored values (nodes with >= 2 keys)              */
+    uint64_t gr_bits;          /* Golomb-Rice bit length                           */
+    uint64_t gr_words;         /* 64-bit words holding them                        */
+    uint64_t ef_words;         /* words of the two Elias-Fano sequences            */
+    uint32_t ef_low_bits[2];   /* L of the key-count / bit-position sequences      */
+    uint64_t ef_seq_words[4];  /* low, high words of sequence 0, then sequence 1   */
+    uint32_t max_bucket;       /* largest bucket seen                              */
+    uint32_t reserved;
+} mphf_info;
+
+/* Work done by the searches, per node kind (0 leaf, 1 lower-1 split, 2 lower-2
+ * split, 3 fanout-2 split): trials = candidate values up to and including the
+ * stored one (one k counts once for rotation leaves); evals = trials * m. */
+typedef struct {
+    uint64_t trials[4];
+    uint64_t evals[4];
+    /* device time: fingerprint/plan up to the first host read, the search
+     * kernel alone, the packing after it, and the whole build */
+    float ms_plan, ms_search, ms_pack, ms_total;
+} mphf_stats;
+
+/* Fills *p with leaf 16, bucket 2000, 8-byte keys, rotation fitting on,
+ * max_value MPHF_DEFAULT_MAX_VALUE, default allocator and launch shape. */
+void mphf_default_params(mphf_build_params *p);
+
+/* Builds the function of the n keys at d_keys (Section 2.2, the whole
+ * construction: fingerprint, bucket sort, split and leaf searches, preorder
+ * Golomb-Rice and Elias-Fano packing, all on the device).  Shorthand for
+ * mphf_build_ex with 8-byte keys and rotation fitting on.  n = 0 gives a
+ * valid empty function.  On success *out owns the result.  Synchronises
+ * the stream. */
+int mphf_build(const void *d_keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size,
+               void *stream, mphf_t **out);
+
+int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *params, void *stream,
+                  mphf_t **out);
+
+/* Same as mphf_build_ex with the keys in host memory: the keys are copied
+ * to the device inside the call (pinned host memory gives the fastest copy). */
+int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *params,
+                    void *stream, mphf_t **out);
+
+/* Evaluates h on n keys (Section 2.2, "Query"; Section 3 for the rotation
+ * of the keys in B).  d_out[i] = h(key i) in [0, n_built) for keys of the
+ * built set.  Asynchronous on the stream. */
+int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out, void *stream);
+
+/* Checks on the device that h maps the n keys at d_keys bijectively onto
+ * [0, n) (queries them, marks a bitmap).  *n_bad = keys whose value was out
+ * of range or already taken; 0 means a bijection.  Synchronises. */
+int mphf_verify(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad, void *stream);
+
+int mphf_get_info(const mphf_t *h, mphf_info *info);
+
+/* Device arrays of a built function, owned by h:
+ *   d_values   n_nodes stored values; bucket i's nodes in preorder at
+ *              [d_node_off[i], d_node_off[i+1]).  A rotation leaf of m keys
+ *              stores k*m + r (seed k*m, rotation r).
+ *   d_node_off nb + 1 offsets.
+ *   d_cum_keys nb + 1 bucket prefix sums of key counts.
+ *   d_bit_pos  nb + 1 start bits of each bucket's Golomb-Rice code. */
+int mphf_get_values(const mphf_t *h, const uint64_t **d_values, const uint64_t **d_node_off,
+                    const uint64_t **d_cum_keys, const uint64_t **d_bit_pos);
+
+/* Packed function: Golomb-Rice words (bit i of the stream is bit i % 64 of
+ * word i / 64) and the Elias-Fano words (low and high words of the key-count
+ * sequence, then of the bit-position sequence). */
+int mphf_get_bits(const mphf_t *h, const uint64_t **d_gr, uint64_t *gr_bits, const uint64_t **d_ef,
+                  uint64_t *ef_words);
+
+int mphf_get_stats(const mphf_t *h, mphf_stats *stats);
+
+/* Golomb-Rice parameter per node size m in [0, max_m] as the library uses it
+ * (Section 2.2, "Representation": one parameter per tree layer, precomputed).
+ * Writes max_m + 1 bytes to host memory. */
+int mphf_tau_table(uint32_t leaf_size, uint32_t rotation_fitting, uint32_t max_m, uint8_t *h_out);
+
+/* Copies the function to host memory: a header then the Golomb-Rice and
+ * Elias-Fano words.  With h_buf NULL, *len receives the size needed. */
+int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream);
+
+int mphf_free(mphf_t *h);
+
+const char *mphf_strerror(int code);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all builds, queries and verifications). */
+uint64_t mphf_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------
+ * Batched builds: many independent functions through one persistent search
+ * launch (buckets of all builds share one device work queue).  Results are
+ * identical to building each alone.  statuses[i] receives each build's code;
+ * the return value is MPHF_OK if all succeeded, else the first failure. */
+typedef struct {
+    const void *d_keys;
+    uint64_t n;
+    uint32_t leaf_size;
+    uint32_t bucket_size;
+    uint32_t key_bytes;
+    uint32_t rotation_fitting;
+    uint64_t max_value;       /* 0 = MPHF_DEFAULT_MAX_VALUE */
+} mphf_build_desc;
+
+int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream, mphf_t **outs,
+                     int *statuses);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPHF_H */

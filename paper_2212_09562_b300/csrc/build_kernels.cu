@@ -1,0 +1,755 @@
+// build_kernels.cu -- device side of one or many RecSplit builds.
+//
+// Stages (Section 2.2 of Bez et al. 2212.09562, parallel form of Section 4.3):
+//   k_fp_hist   master hash of every key, bucket histogram
+//   k_plan      stored-node count per bucket (from the bucket size alone)
+//   k_scan_*    exclusive prefix sums (bucket offsets, node offsets, bits)
+//   k_scatter   keys grouped by bucket (lo word + rotation bit)
+//   k_search    persistent kernel, one block per bucket at a time: split
+//               searches of the inner nodes (all threads of the block try
+//               consecutive seeds), redistribution in shared memory, then
+//               leaf searches with one warp per leaf (plain or rotation
+//               fitting, Section 3)
+//   k_gr_*      Golomb-Rice lengths and bit writes (fixed parts, then unary
+//               parts, in preorder per bucket)
+//   k_ef_*      Elias-Fano sequences and a rank directory for select
+//   k_stats     trial / hash-evaluation counts from the stored values
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace rs {
+
+__device__ __forceinline__ void load_key(const void *keys, uint64_t i, uint32_t kb, uint64_t &w0,
+                                         uint64_t &w1) {
+    const uint64_t *p = (const uint64_t *)keys;
+    if (kb == 8) {
+        w0 = p[i];
+        w1 = 0;
+    } else {
+        w0 = p[2 * i];
+        w1 = p[2 * i + 1];
+    }
+}
+
+static unsigned long long g_launches = 0;
+void note_launches(uint64_t k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+uint64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+static uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t cap = 148u * 32u) {
+    uint64_t g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    return g ? (uint32_t)g : 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Fingerprint + bucket histogram.
+__global__ void k_fp_hist(const void *keys, uint64_t n, uint32_t kb, uint64_t nb,
+                          unsigned long long *counts) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t w0, w1, hi, lo;
+        load_key(keys, i, kb, w0, w1);
+        fingerprint(w0, w1, hi, lo);
+        atomicAdd(&counts[mulhi64(hi, nb)], 1ull);
+    }
+}
+
+void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint64_t *counts,
+                    cudaStream_t st) {
+    if (n == 0) return;
+    k_fp_hist<<<grid_for(n, 256), 256, 0, st>>>(keys, n, key_bytes, nb, (unsigned long long *)counts);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Plan: nodes per bucket, oversized buckets, largest bucket.
+__global__ void k_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab,
+                       uint64_t *node_cnt, uint32_t *status, uint32_t *max_m) {
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nb;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t m = counts[b];
+        if (m > 4096) {
+            atomicOr(status, ST_BUCKET);
+            node_cnt[b] = 0;
+        } else {
+            node_cnt[b] = nodes_tab[m];
+        }
+        atomicMax(max_m, (uint32_t)(m > 0xFFFFFFFFull ? 0xFFFFFFFFull : m));
+    }
+}
+
+void launch_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab, uint64_t *node_cnt,
+                 uint32_t *status, uint32_t *max_m, cudaStream_t st) {
+    if (nb == 0) return;
+    k_plan<<<grid_for(nb, 256), 256, 0, st>>>(counts, nb, nodes_tab, node_cnt, status, max_m);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan, reduce-then-scan over tiles of 2048 values.
+constexpr uint32_t SCAN_T = 256, SCAN_PER = 8, SCAN_TILE = SCAN_T * SCAN_PER;
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v) {
+    uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= (uint32_t)d) v += o;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the prefix,
+// *total receives the block sum.
+__device__ uint64_t block_excl_scan(uint64_t v, uint64_t *total) {
+    __shared__ uint64_t warp_sums[32];
+    uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    uint64_t incl = warp_incl_scan(v);
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t s = lane < nw ? warp_sums[lane] : 0;
+        uint64_t si = warp_incl_scan(s);
+        if (lane < nw) warp_sums[lane] = si - s;
+        if (lane == nw - 1) warp_sums[31] = si;
+    }
+    __syncthreads();
+    uint64_t r = warp_sums[warp] + incl - v;
+    if (total) *total = warp_sums[31];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint64_t *d, uint64_t len, uint64_t *sums) {
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    uint64_t s = 0;
+    for (uint32_t j = 0; j < SCAN_PER; j++) {
+        uint64_t i = base + (uint64_t)j * SCAN_T + threadIdx.x;
+        if (i < len) s += d[i];
+    }
+    uint64_t total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_apply(uint64_t *d, uint64_t len, const uint64_t *offs) {
+    uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_PER;
+    uint64_t v[SCAN_PER];
+    uint64_t s = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < SCAN_PER; j++) {
+        v[j] = base + j < len ? d[base + j] : 0;
+        s += v[j];
+    }
+    uint64_t pre = block_excl_scan(s, nullptr) + (offs ? offs[blockIdx.x] : 0);
+#pragma unroll
+    for (uint32_t j = 0; j < SCAN_PER; j++) {
+        if (base + j < len) d[base + j] = pre;
+        pre += v[j];
+    }
+}
+
+uint64_t scan_tmp_words(uint64_t len) {
+    uint64_t tiles = (len + SCAN_TILE - 1) / SCAN_TILE;
+    return tiles <= 1 ? 1 : tiles + scan_tmp_words(tiles);
+}
+
+void launch_exclusive_scan(uint64_t *data, uint64_t len, uint64_t *tmp, cudaStream_t st) {
+    if (len == 0) return;
+    uint64_t tiles = (len + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 1) {
+        k_scan_apply<<<1, SCAN_T, 0, st>>>(data, len, nullptr);
+        note_launches(1);
+        return;
+    }
+    k_scan_reduce<<<(uint32_t)tiles, SCAN_T, 0, st>>>(data, len, tmp);
+    note_launches(1);
+    launch_exclusive_scan(tmp, tiles, tmp + tiles, st);
+    k_scan_apply<<<(uint32_t)tiles, SCAN_T, 0, st>>>(data, len, tmp);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Scatter: lo word and rotation bit of every key to its bucket's range.
+__global__ void k_scatter(const void *keys, uint64_t n, uint32_t kb, uint64_t nb,
+                          const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo_out,
+                          uint8_t *bb_out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t w0, w1, hi, lo;
+        load_key(keys, i, kb, w0, w1);
+        fingerprint(w0, w1, hi, lo);
+        uint64_t b = mulhi64(hi, nb);
+        uint64_t p = bucket_off[b] + atomicAdd(&cursor[b], 1u);
+        lo_out[p] = lo;
+        bb_out[p] = (uint8_t)(hi & 1);
+    }
+}
+
+void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                    const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo, uint8_t *bb,
+                    cudaStream_t st) {
+    if (n == 0) return;
+    k_scatter<<<grid_for(n, 256), 256, 0, st>>>(keys, n, key_bytes, nb, bucket_off, cursor, lo, bb);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// The search kernel.
+constexpr int STACK = 64;
+
+struct BlockState {
+    uint16_t st_off[STACK], st_m[STACK], st_pidx[STACK];
+    uint8_t st_depth[STACK];
+    int sp;
+    uint32_t nleaves, leaf_next, flags, item;
+    unsigned long long found;
+    uint32_t cnt[16];
+};
+
+struct SmemArrays {
+    uint64_t *lo, *tlo;
+    uint8_t *bb, *tbb;
+    uint16_t *leaf_off, *leaf_pidx;
+    uint8_t *leaf_m;
+};
+
+// Number of bits of x (x >= 1): the packed-counter field width for parts <= x.
+__host__ __device__ constexpr uint32_t bit_width_ce(uint32_t x) { return x ? 1 + bit_width_ce(x >> 1) : 0; }
+
+template <uint32_t U>
+struct DivCT {
+    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return p / U; }
+};
+struct DivRT {
+    uint32_t magic;
+    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return div_unit(p, magic); }
+};
+
+// Lower aggregation split: all threads of the block test consecutive seeds;
+// counts are packed w-bit fields, one per child, compared with the target word.
+// The whole chunk of seeds is decided before the next one starts, so the
+// smallest working seed wins.
+template <class Mod, class Div>
+__device__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div, uint32_t w,
+                                 uint64_t expected, uint64_t maxv, bool &limit, BlockState &S) {
+    const uint32_t T = blockDim.x;
+    for (uint64_t base = 0;; base += T) {
+        uint64_t s = base + threadIdx.x;
+        uint64_t cnt = 0;
+#pragma unroll 4
+        for (uint32_t i = 0; i < m; i++) {
+            uint32_t p = mod(mix64(xs[i] + s));
+            cnt += 1ull << (w * div(p));
+        }
+        bool ok = cnt == expected && s <= maxv;
+        if (__syncthreads_or(ok)) {
+            if (ok) atomicMin(&S.found, (unsigned long long)s);
+            __syncthreads();
+            return S.found;
+        }
+        if (base + T > maxv) {
+            limit = true;
+            return 0;
+        }
+    }
+}
+
+// Fanout-2 split: one counter of keys hashed below `left`.
+template <class Mod>
+__device__ uint64_t search_upper(const uint64_t *xs, uint32_t m, Mod mod, uint32_t left,
+                                 uint64_t maxv, bool &limit, BlockState &S) {
+    const uint32_t T = blockDim.x;
+    for (uint64_t base = 0;; base += T) {
+        uint64_t s = base + threadIdx.x;
+        uint32_t cnt = 0;
+#pragma unroll 4
+        for (uint32_t i = 0; i < m; i++) cnt += mod(mix64(xs[i] + s)) < left;
+        bool ok = cnt == left && s <= maxv;
+        if (__syncthreads_or(ok)) {
+            if (ok) atomicMin(&S.found, (unsigned long long)s);
+            __syncthreads();
+            return S.found;
+        }
+        if (base + T > maxv) {
+            limit = true;
+            return 0;
+        }
+    }
+}
+
+// Leaf, plain brute force (Section 2.2 "Bijections"): one warp, lane = seed.
+template <class Mod>
+__device__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, Mod mod, uint64_t maxv, bool &limit,
+                               uint32_t lane) {
+    const uint32_t full = (1u << m) - 1;
+    for (uint64_t s0 = 0;; s0 += 32) {
+        uint64_t s = s0 + lane;
+        uint32_t mask = 0;
+        for (uint32_t i = 0; i < m; i++) mask |= 1u << mod(mix64(xs[i] + s));
+        uint32_t ball = __ballot_sync(0xffffffffu, mask == full);
+        if (ball) {
+            uint64_t x = s0 + (uint32_t)(__ffs(ball) - 1);
+            if (x > maxv) limit = true;
+            return x;
+        }
+        if (s0 + 32 > maxv) {
+            limit = true;
+            return 0;
+        }
+    }
+}
+
+// Leaf with rotation fitting (Section 3): lane = k, seed k*m; keys of A set
+// bits of a, keys of B bits of b; the smallest r with a | rot_m^r(b) full.
+// The lowest lane with a hit has the smallest k, hence the smallest k*m + r.
+template <class Mod>
+__device__ uint64_t leaf_rotation(const uint64_t *xs, const uint8_t *bbs, uint32_t m, Mod mod,
+                                  uint64_t maxv, bool &limit, uint32_t lane) {
+    const uint32_t full = (1u << m) - 1;
+    uint32_t nb = 0;
+    for (uint32_t i = 0; i < m; i++) nb += bbs[i];
+    const uint32_t na = m - nb;
+    for (uint64_t k0 = 0;; k0 += 32) {
+        uint64_t s = (k0 + lane) * m;
+        uint32_t a = 0, b = 0;
+        for (uint32_t i = 0; i < m; i++) {
+            uint32_t bit = 1u << mod(mix64(xs[i] + s));
+            if (bbs[i])
+                b |= bit;
+            else
+                a |= bit;
+        }
+        int rf = -1;
+        if (__popc(a) == (int)na && __popc(b) == (int)nb) {
+            for (uint32_t r = 0; r < m; r++) {
+                uint32_t rot = r == 0 ? b : (((b << r) | (b >> (m - r))) & full);
+                if ((a | rot) == full) {
+                    rf = (int)r;
+                    break;
+                }
+            }
+        }
+        uint32_t ball = __ballot_sync(0xffffffffu, rf >= 0);
+        if (ball) {
+            uint64_t x = __shfl_sync(0xffffffffu, s + (uint64_t)(rf < 0 ? 0 : rf), __ffs(ball) - 1);
+            if (x > maxv) limit = true;
+            return x;
+        }
+        if ((k0 + 32) * m > maxv) {
+            limit = true;
+            return 0;
+        }
+    }
+}
+
+// Any two equal lo words among keys [0, m) of the block's bucket.
+__device__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
+    bool dup = false;
+    for (uint32_t i = threadIdx.x; i < m && !dup; i += blockDim.x)
+        for (uint32_t j = i + 1; j < m; j++)
+            if (lo[i] == lo[j]) {
+                dup = true;
+                break;
+            }
+    return __syncthreads_or(dup);
+}
+
+template <int LEAF>
+__device__ void split_node(const InstDesc &d, const Shape &sh, uint32_t off, uint32_t m,
+                           uint32_t depth, uint32_t pidx, uint64_t nbase, uint32_t bucket_m,
+                           const SmemArrays &A, BlockState &S) {
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    const uint32_t kind = node_kind(sh, m);
+    const uint64_t salt = level_salt(salt_level(sh, m, depth));
+    for (uint32_t i = tid; i < m; i += T) A.tlo[off + i] = A.lo[off + i] + salt;
+    if (tid == 0) S.found = ~0ull;
+    __syncthreads();
+    const uint64_t *xs = A.tlo + off;
+    const uint32_t np = num_parts(sh, m);
+    uint64_t x = 0;
+    bool limit = false;
+    const ModRT mrt = make_mod(m);
+    if (kind == NODE_UPPER) {
+        x = search_upper(xs, m, mrt, upper_left(sh, m), d.max_value, limit, S);
+    } else {
+        const uint32_t unit = lower_unit(sh, m);
+        const uint32_t w = counter_width(unit);
+        uint64_t expected = 0;
+        for (uint32_t c = 0; c < np; c++) expected += (uint64_t)part_size(sh, m, c) << (w * c);
+        if constexpr (LEAF != 0) {
+            // full lower-1 and lower-2 nodes: compile-time modulus, unit and field width
+            constexpr uint32_t f1 = ((35u * LEAF + 154u) / 100u) < 2 ? 2 : (35u * LEAF + 154u) / 100u;
+            constexpr uint32_t f2 = ((21u * LEAF + 189u) / 100u) < 2 ? 2 : (21u * LEAF + 189u) / 100u;
+            constexpr uint32_t L1 = f1 * LEAF, L2 = f2 * L1;
+            constexpr uint32_t W1 = bit_width_ce(LEAF), W2 = bit_width_ce(L1);
+            if (m == L1) {
+                x = search_lower(xs, m, ModCT<L1>(), DivCT<LEAF>(), W1, expected, d.max_value,
+                                 limit, S);
+            } else if (m == L2) {
+                x = search_lower(xs, m, ModCT<L2>(), DivCT<L1>(), W2, expected, d.max_value,
+                                 limit, S);
+            } else {
+                x = search_lower(xs, m, mrt, DivRT{unit_magic(unit)}, w, expected, d.max_value,
+                                 limit, S);
+            }
+        } else {
+            x = search_lower(xs, m, mrt, DivRT{unit_magic(unit)}, w, expected, d.max_value, limit,
+                             S);
+        }
+    }
+    if (limit) {  // uniform: decided after a block-wide vote
+        bool dup = block_has_duplicate(A.lo, bucket_m);
+        if (tid == 0) S.flags |= dup ? ST_DUPLICATE : ST_LIMIT;
+        __syncthreads();
+        return;
+    }
+    if (tid == 0) {
+        d.values[nbase + pidx] = x;
+        d.node_m[nbase + pidx] = (uint16_t)m;
+    }
+    // regroup the node's keys by child with the seed found
+    if (tid < np) S.cnt[tid] = 0;
+    __syncthreads();
+    const bool upper = kind == NODE_UPPER;
+    const uint32_t left = upper ? upper_left(sh, m) : 0;
+    const uint32_t unit = upper ? 1 : lower_unit(sh, m);
+    const uint32_t um = upper ? 0 : unit_magic(unit);
+    for (uint32_t i = tid; i < m; i += T) {
+        uint32_t p = mrt(mix64(xs[i] + x));
+        uint32_t c = upper ? (p < left ? 0u : 1u) : div_unit(p, um);
+        uint32_t start = upper ? (c ? left : 0u) : c * unit;
+        uint32_t dst = off + start + atomicAdd(&S.cnt[c], 1u);
+        A.lo[dst] = xs[i] - salt;
+        A.tbb[dst] = A.bb[off + i];
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < m; i += T) A.bb[off + i] = A.tbb[off + i];
+    if (tid == 0) {
+        uint32_t coff = off, cp = pidx + 1;
+        for (uint32_t c = 0; c < np; c++) {
+            uint32_t q = part_size(sh, m, c);
+            if (q >= 2) {
+                if (q <= sh.leaf) {
+                    uint32_t j = S.nleaves++;
+                    A.leaf_off[j] = (uint16_t)coff;
+                    A.leaf_m[j] = (uint8_t)q;
+                    A.leaf_pidx[j] = (uint16_t)cp;
+                } else {
+                    int k = S.sp++;
+                    S.st_off[k] = (uint16_t)coff;
+                    S.st_m[k] = (uint16_t)q;
+                    S.st_depth[k] = (uint8_t)(depth + 1);
+                    S.st_pidx[k] = (uint16_t)cp;
+                }
+            }
+            cp += d.nodes_tab[q];
+            coff += q;
+        }
+    }
+    __syncthreads();
+}
+
+template <int LEAF>
+__device__ void leaf_phase(const InstDesc &d, uint64_t nbase, const SmemArrays &A, BlockState &S) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t salt = level_salt(0);
+    for (;;) {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(&S.leaf_next, 1u);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        if (j >= S.nleaves) break;
+        const uint32_t off = A.leaf_off[j], m = A.leaf_m[j];
+        // equal lo words can never be separated: refuse the bucket
+        bool dup = false;
+        if (lane < m)
+            for (uint32_t i = lane + 1; i < m; i++) dup |= A.lo[off + lane] == A.lo[off + i];
+        if (__any_sync(0xffffffffu, dup)) {
+            if (lane == 0) atomicOr(&S.flags, ST_DUPLICATE);
+            continue;
+        }
+        if (lane < m) A.tlo[off + lane] = A.lo[off + lane] + salt;
+        __syncwarp();
+        const uint64_t *xs = A.tlo + off;
+        bool limit = false;
+        uint64_t x;
+        bool done = false;
+        if constexpr (LEAF != 0) {
+            if (m == (uint32_t)LEAF) {  // full leaf: compile-time modulus
+                x = d.rotation ? leaf_rotation(xs, A.bb + off, m, ModCT<LEAF>(), d.max_value, limit, lane)
+                               : leaf_plain(xs, m, ModCT<LEAF>(), d.max_value, limit, lane);
+                done = true;
+            }
+        }
+        if (!done)
+            x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_mod(m), d.max_value, limit, lane)
+                           : leaf_plain(xs, m, make_mod(m), d.max_value, limit, lane);
+        if (lane == 0) {
+            if (limit) {
+                atomicOr(&S.flags, ST_LIMIT);
+            } else {
+                d.values[nbase + A.leaf_pidx[j]] = x;
+                d.node_m[nbase + A.leaf_pidx[j]] = (uint16_t)m;
+            }
+        }
+    }
+}
+
+template <int LEAF>
+__device__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
+                               BlockState &S) {
+    const uint32_t tid = threadIdx.x, T = blockDim.x;
+    const Shape sh = make_shape(LEAF ? (uint32_t)LEAF : d.leaf);
+    const uint64_t kbeg = d.bucket_off[bucket];
+    const uint64_t M = d.bucket_off[bucket + 1] - kbeg;
+    const uint64_t nbase = d.node_off[bucket];
+    if (M <= 1 || M > 4096) return;  // nothing stored / refused by the plan
+    for (uint32_t i = tid; i < M; i += T) {
+        A.lo[i] = d.lo[kbeg + i];
+        A.bb[i] = d.bb[kbeg + i];
+    }
+    if (tid == 0) {
+        S.sp = 0;
+        S.nleaves = 0;
+        S.leaf_next = 0;
+        S.flags = 0;
+        if (M <= sh.leaf) {
+            A.leaf_off[0] = 0;
+            A.leaf_m[0] = (uint8_t)M;
+            A.leaf_pidx[0] = 0;
+            S.nleaves = 1;
+        } else {
+            S.st_off[0] = 0;
+            S.st_m[0] = (uint16_t)M;
+            S.st_depth[0] = 0;
+            S.st_pidx[0] = 0;
+            S.sp = 1;
+        }
+    }
+    __syncthreads();
+    for (;;) {
+        if (S.sp == 0 || S.flags) break;
+        const int k = S.sp - 1;
+        const uint32_t off = S.st_off[k], m = S.st_m[k], depth = S.st_depth[k], pidx = S.st_pidx[k];
+        __syncthreads();
+        if (tid == 0) S.sp = k;
+        split_node<LEAF>(d, sh, off, m, depth, pidx, nbase, (uint32_t)M, A, S);
+    }
+    if (!S.flags) leaf_phase<LEAF>(d, nbase, A, S);
+    __syncthreads();
+    if (tid == 0 && S.flags) atomicOr(d.status, S.flags);
+    __syncthreads();
+}
+
+// Dynamic shared memory of the search kernel for buckets of at most `cap`
+// keys.  The capacity is padded to 16 so that every array starts aligned:
+// lo, tlo at 0 and 8P (u64), bb, tbb at 16P and 17P (u8), the leaf list at
+// 18P (two u16 arrays of nl entries, then nl bytes).
+struct SmemLayout {
+    uint32_t P, nl, bytes;
+    __host__ __device__ explicit SmemLayout(uint32_t cap) {
+        P = (cap + 15u) & ~15u;
+        nl = P / 2 + 1;
+        bytes = 18u * P + 5u * nl;
+    }
+};
+
+__global__ void __launch_bounds__(512) k_search(const InstDesc *insts, const WorkItem *items,
+                                                uint32_t nitems, uint32_t *head, uint32_t cap) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ BlockState S;
+    const SmemLayout lay(cap);
+    SmemArrays A;
+    A.lo = (uint64_t *)dyn;
+    A.tlo = A.lo + lay.P;
+    A.bb = dyn + 16u * lay.P;
+    A.tbb = A.bb + lay.P;
+    A.leaf_off = (uint16_t *)(dyn + 18u * lay.P);
+    A.leaf_pidx = A.leaf_off + lay.nl;
+    A.leaf_m = (uint8_t *)(A.leaf_pidx + lay.nl);
+    for (;;) {
+        if (threadIdx.x == 0) S.item = atomicAdd(head, 1u);
+        __syncthreads();
+        const uint32_t it = S.item;
+        __syncthreads();
+        if (it >= nitems) break;
+        const WorkItem w = items[it];
+        const InstDesc d = insts[w.inst];
+        switch (d.leaf) {
+            case 8: process_bucket<8>(d, w.bucket, A, S); break;
+            case 12: process_bucket<12>(d, w.bucket, A, S); break;
+            case 16: process_bucket<16>(d, w.bucket, A, S); break;
+            default: process_bucket<0>(d, w.bucket, A, S); break;
+        }
+    }
+}
+
+static uint32_t search_smem(uint32_t cap) { return SmemLayout(cap).bytes; }
+
+SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads,
+                                uint32_t blocks_per_sm) {
+    SearchLaunch L;
+    L.cap = max_m < 2 ? 2 : max_m;
+    L.threads = threads ? threads : 256;
+    L.smem_bytes = search_smem(L.cap);
+    int dev = 0, sms = 148, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, L.threads, L.smem_bytes);
+    if (occ < 1) occ = 1;
+    uint32_t per_sm = blocks_per_sm ? (blocks_per_sm < (uint32_t)occ ? blocks_per_sm : occ) : occ;
+    uint64_t g = (uint64_t)sms * per_sm;
+    if (g > items) g = items;
+    L.blocks = g ? (uint32_t)g : 1;
+    return L;
+}
+
+void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
+                   const SearchLaunch &L, cudaStream_t st) {
+    if (items == 0) return;
+    k_search<<<L.blocks, L.threads, L.smem_bytes, st>>>(d_inst, d_items, items, d_head, L.cap);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Golomb-Rice: per-bucket lengths, then the bits (one warp per bucket).
+__global__ void k_gr_len(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
+                         uint64_t nb, const uint8_t *tau, uint64_t *bucket_bits) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b = warp; b < nb; b += nwarps) {
+        uint64_t bits = 0;
+        for (uint64_t j = node_off[b] + lane; j < node_off[b + 1]; j += 32) {
+            uint32_t t = tau[node_m[j]];
+            bits += t + 1 + (values[j] >> t);
+        }
+        for (int d = 16; d; d >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, d);
+        if (lane == 0) bucket_bits[b] = bits;
+    }
+}
+
+void launch_gr_lengths(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
+                       uint64_t nb, const uint8_t *tau, uint64_t *bucket_bits, cudaStream_t st) {
+    if (nb == 0) return;
+    k_gr_len<<<grid_for(nb * 32, 256), 256, 0, st>>>(values, node_m, node_off, nb, tau, bucket_bits);
+    note_launches(1);
+}
+
+__device__ __forceinline__ void or_bits(uint64_t *w, uint64_t pos, uint64_t v, uint32_t len) {
+    if (len == 0 || v == 0) return;
+    uint32_t sh = (uint32_t)(pos & 63);
+    atomicOr((unsigned long long *)&w[pos >> 6], (unsigned long long)(v << sh));
+    if (sh + len > 64) atomicOr((unsigned long long *)&w[(pos >> 6) + 1], (unsigned long long)(v >> (64 - sh)));
+}
+
+__global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
+                           const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
+                           const uint32_t *fixed_tab, const uint64_t *bucket_off, uint64_t *gr) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b = warp; b < nb; b += nwarps) {
+        const uint64_t m = bucket_off[b + 1] - bucket_off[b];
+        const uint64_t start = bit_pos[b];
+        const uint64_t ustart = start + fixed_tab[m <= 4096 ? m : 0];
+        uint64_t frun = 0, urun = 0;
+        for (uint64_t j0 = node_off[b]; j0 < node_off[b + 1]; j0 += 32) {
+            const uint64_t j = j0 + lane;
+            const bool valid = j < node_off[b + 1];
+            const uint32_t t = valid ? tau[node_m[j]] : 0;
+            const uint64_t x = valid ? values[j] : 0;
+            const uint64_t ulen = valid ? (x >> t) + 1 : 0;
+            const uint64_t it = warp_incl_scan(t), iu = warp_incl_scan(ulen);
+            if (valid) {
+                uint64_t fx = t ? (x & ((t == 64) ? ~0ull : ((1ull << t) - 1))) : 0;
+                or_bits(gr, start + frun + it - t, fx, t);
+                uint64_t up = ustart + urun + iu - 1;
+                atomicOr((unsigned long long *)&gr[up >> 6], 1ull << (up & 63));
+            }
+            frun += __shfl_sync(0xffffffffu, it, 31);
+            urun += __shfl_sync(0xffffffffu, iu, 31);
+        }
+    }
+}
+
+void launch_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
+                     const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
+                     const uint32_t *fixed_tab, const uint64_t *bucket_off, uint64_t *gr,
+                     cudaStream_t st) {
+    if (nb == 0) return;
+    k_gr_write<<<grid_for(nb * 32, 256), 256, 0, st>>>(values, node_m, node_off, bit_pos, nb, tau,
+                                                         fixed_tab, bucket_off, gr);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Elias-Fano (Section 2.1): low L bits of v_i at [iL, iL + L), a one at
+// (v_i >> L) + i in the high bits.
+__global__ void k_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low,
+                           uint64_t *high) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < k;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x = v[i];
+        if (L) or_bits(low, i * L, x & ((L == 64) ? ~0ull : ((1ull << L) - 1)), L);
+        uint64_t hb = (x >> L) + i;
+        atomicOr((unsigned long long *)&high[hb >> 6], 1ull << (hb & 63));
+    }
+}
+
+void launch_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low, uint64_t *high,
+                     cudaStream_t st) {
+    if (k == 0) return;
+    k_ef_write<<<grid_for(k, 256), 256, 0, st>>>(v, k, L, low, high);
+    note_launches(1);
+}
+
+__global__ void k_popcount(const uint64_t *words, uint64_t n, uint64_t *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = __popcll(words[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = 0;
+}
+
+// Stats: trials up to the stored value, and hash evaluations, per node kind.
+__global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes,
+                        uint32_t leaf, uint32_t rotation, unsigned long long *counters) {
+    __shared__ unsigned long long acc[8];
+    if (threadIdx.x < 8) acc[threadIdx.x] = 0;
+    __syncthreads();
+    const Shape sh = make_shape(leaf);
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n_nodes;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t m = node_m[j];
+        uint32_t kind = node_kind(sh, m);
+        uint64_t x = values[j];
+        uint64_t trials = (kind == NODE_LEAF && rotation) ? x / m + 1 : x + 1;
+        uint32_t idx = kind == NODE_LEAF ? 0 : kind == NODE_LOWER1 ? 1 : kind == NODE_LOWER2 ? 2 : 3;
+        atomicAdd(&acc[idx], (unsigned long long)trials);
+        atomicAdd(&acc[4 + idx], (unsigned long long)(trials * m));
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) atomicAdd(&counters[threadIdx.x], acc[threadIdx.x]);
+}
+
+void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
+                  uint32_t rotation, uint64_t *counters, cudaStream_t st) {
+    if (n_nodes == 0) return;
+    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, leaf, rotation,
+                                                          (unsigned long long *)counters);
+    note_launches(1);
+}
+
+// Rank directory of a bit vector: out[w] = ones in words [0, w) (select support).
+void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint64_t *tmp,
+                     cudaStream_t st) {
+    k_popcount<<<grid_for(nwords + 1, 256), 256, 0, st>>>(words, nwords, dir);
+    note_launches(1);
+    launch_exclusive_scan(dir, nwords + 1, tmp, st);
+}
+
+}  // namespace rs

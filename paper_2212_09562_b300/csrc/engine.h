@@ -1,0 +1,88 @@
+// engine.h -- internal interface between the C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rs {
+
+// Device status bits of one build (host maps them to error codes with the
+// precedence bucket size > duplicate > search cap > wait timeout).
+enum : uint32_t { ST_BUCKET = 1u, ST_DUPLICATE = 2u, ST_LIMIT = 4u, ST_TIMEOUT = 8u };
+
+// Per-build descriptor read by the search kernel (one per instance of a batch).
+struct InstDesc {
+    const uint64_t *lo;          // fingerprint lo words, grouped by bucket
+    const uint8_t *bb;           // B bit (hi & 1) of the same keys
+    const uint64_t *bucket_off;  // nb + 1 key offsets
+    const uint64_t *node_off;    // nb + 1 node offsets
+    const uint32_t *nodes_tab;   // stored nodes per subtree size
+    uint64_t *values;            // node values, preorder per bucket
+    uint16_t *node_m;            // node sizes, same order
+    uint32_t *status;            // ST_* bits
+    uint64_t max_value;
+    uint32_t leaf, rotation;
+    uint32_t nb, pad;
+};
+
+// One unit of work: a bucket of an instance.
+struct WorkItem {
+    uint32_t inst, bucket;
+};
+
+struct SearchLaunch {
+    uint32_t threads;        // per block
+    uint32_t blocks;         // persistent grid size
+    uint32_t smem_bytes;     // dynamic shared memory
+    uint32_t cap;            // largest bucket the blocks hold
+};
+
+// Kernels launched by this library in this process (every launcher adds its count).
+void note_launches(uint64_t k);
+uint64_t launches_total();
+
+// Stage launchers (all asynchronous on `st`).
+void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint64_t *counts,
+                    cudaStream_t st);
+void launch_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab, uint64_t *node_cnt,
+                 uint32_t *status, uint32_t *max_m, cudaStream_t st);
+// Exclusive scan of n + 1 values in place (the last input should be 0; the
+// last output is then the total).  tmp needs scan_tmp_words(n + 1) words.
+uint64_t scan_tmp_words(uint64_t len);
+void launch_exclusive_scan(uint64_t *data, uint64_t len, uint64_t *tmp, cudaStream_t st);
+void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                    const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo, uint8_t *bb,
+                    cudaStream_t st);
+SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads, uint32_t blocks_per_sm);
+void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
+                   const SearchLaunch &L, cudaStream_t st);
+void launch_gr_lengths(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
+                       uint64_t nb, const uint8_t *tau, uint64_t *bucket_bits, cudaStream_t st);
+void launch_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
+                     const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
+                     const uint32_t *fixed_tab, const uint64_t *bucket_off, uint64_t *gr,
+                     cudaStream_t st);
+void launch_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low, uint64_t *high,
+                     cudaStream_t st);
+// dir[w] = ones in words [0, w), w in [0, nwords]; tmp: scan_tmp_words(nwords + 1).
+void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint64_t *tmp,
+                     cudaStream_t st);
+void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
+                  uint32_t rotation, uint64_t *counters, cudaStream_t st);
+
+// Query side.
+struct QueryView {
+    const uint64_t *gr;
+    const uint64_t *ef_low[2], *ef_high[2];
+    const uint64_t *ef_dir[2];
+    uint64_t ef_high_words[2];
+    uint32_t ef_L[2];
+    const uint8_t *tau;
+    const uint32_t *nodes_tab, *fixed_tab;
+    uint64_t nb;
+    uint32_t leaf, rotation, key_bytes, pad;
+};
+void launch_query(const QueryView &q, const void *keys, uint64_t n, uint64_t *out, cudaStream_t st);
+void launch_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad,
+                 cudaStream_t st);
+
+}  // namespace rs

@@ -1,0 +1,160 @@
+// query_kernels.cu -- evaluation of a built function on the device.
+//
+// Section 2.2 ("Query"): bucket of the key, two Elias-Fano lookups (keys
+// before the bucket, start bit of its code), then a walk from the root:
+// decode the node's value (fixed part in the bucket's fixed region, unary
+// part found by select in its unary region), hash to the child, add the
+// sizes of the children to its left and skip their subtrees (per-size
+// tables give their node counts and fixed bits).  At the leaf: the position
+// under the leaf's seed, plus the rotation r mod m for keys of B (Section 3).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "engine.h"
+
+namespace rs {
+
+__device__ __forceinline__ uint64_t read_bits(const uint64_t *w, uint64_t pos, uint32_t len) {
+    if (len == 0) return 0;
+    uint32_t sh = (uint32_t)(pos & 63);
+    uint64_t v = w[pos >> 6] >> sh;
+    if (sh + len > 64) v |= w[(pos >> 6) + 1] << (64 - sh);
+    return len == 64 ? v : v & ((1ull << len) - 1);
+}
+
+// Position of the j-th one (0-based) at or after bit `start`.
+__device__ __forceinline__ uint64_t select_from(const uint64_t *w, uint64_t start, uint64_t j) {
+    uint64_t wi = start >> 6;
+    uint64_t word = w[wi] & (~0ull << (start & 63));
+    for (;;) {
+        uint32_t c = __popcll(word);
+        if (j < c) {
+            for (; j; j--) word &= word - 1;
+            return wi * 64 + (uint64_t)(__ffsll((long long)word) - 1);
+        }
+        j -= c;
+        word = w[++wi];
+    }
+}
+
+// Element i of an Elias-Fano sequence, select on the high bits through the
+// rank directory dir (ones before each word).
+__device__ __forceinline__ uint64_t ef_get(const uint64_t *low, const uint64_t *high,
+                                           const uint64_t *dir, uint64_t nwords, uint32_t L,
+                                           uint64_t i) {
+    uint64_t a = 0, b = nwords - 1;
+    while (a < b) {
+        uint64_t mid = (a + b + 1) >> 1;
+        if (dir[mid] <= i)
+            a = mid;
+        else
+            b = mid - 1;
+    }
+    uint64_t word = high[a];
+    for (uint64_t r = i - dir[a]; r; r--) word &= word - 1;
+    uint64_t sel = a * 64 + (uint64_t)(__ffsll((long long)word) - 1);
+    return ((sel - i) << L) | read_bits(low, i * L, L);
+}
+
+__device__ __forceinline__ uint64_t node_value(const uint64_t *gr, uint64_t fixed_pos, uint32_t tau,
+                                               uint64_t ustart, uint64_t idx) {
+    uint64_t fixed = read_bits(gr, fixed_pos, tau);
+    uint64_t end = select_from(gr, ustart, idx);
+    uint64_t begin = idx == 0 ? ustart : select_from(gr, ustart, idx - 1) + 1;
+    return ((end - begin) << tau) | fixed;
+}
+
+__global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out) {
+    const Shape sh = make_shape(q.leaf);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t *p = (const uint64_t *)keys;
+        uint64_t w0 = q.key_bytes == 8 ? p[i] : p[2 * i];
+        uint64_t w1 = q.key_bytes == 8 ? 0 : p[2 * i + 1];
+        uint64_t hi, lo;
+        fingerprint(w0, w1, hi, lo);
+        uint64_t b = mulhi64(hi, q.nb);
+        uint64_t cum = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_high_words[0], q.ef_L[0], b);
+        uint64_t nxt = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_high_words[0], q.ef_L[0], b + 1);
+        uint64_t start = ef_get(q.ef_low[1], q.ef_high[1], q.ef_dir[1], q.ef_high_words[1], q.ef_L[1], b);
+        uint32_t m = (uint32_t)(nxt - cum);
+        if (m > 4096) {  // not a key of the built set (or a corrupt function)
+            out[i] = cum;
+            continue;
+        }
+        const uint64_t ustart = start + q.fixed_tab[m];
+        uint64_t fpos = start, idx = 0, rank = 0;
+        uint32_t depth = 0;
+        while (m > sh.leaf) {
+            uint32_t t = q.tau[m];
+            uint64_t x = node_value(q.gr, fpos, t, ustart, idx);
+            uint32_t pos = make_mod(m)(mix64(lo + level_salt(salt_level(sh, m, depth)) + x));
+            uint32_t c;
+            if (m > sh.lower2)
+                c = pos < upper_left(sh, m) ? 0 : 1;
+            else
+                c = pos / lower_unit(sh, m);
+            fpos += t;
+            idx += 1;
+            for (uint32_t j = 0; j < c; j++) {
+                uint32_t qj = part_size(sh, m, j);
+                rank += qj;
+                fpos += q.fixed_tab[qj];
+                idx += q.nodes_tab[qj];
+            }
+            m = part_size(sh, m, c);
+            depth++;
+        }
+        if (m <= 1) {
+            out[i] = cum + rank;
+            continue;
+        }
+        uint64_t x = node_value(q.gr, fpos, q.tau[m], ustart, idx);
+        const ModRT mod = make_mod(m);
+        uint64_t pos;
+        if (!q.rotation) {
+            pos = mod(mix64(lo + level_salt(0) + x));
+        } else {
+            uint64_t r = x % m;
+            pos = mod(mix64(lo + level_salt(0) + (x - r)));
+            if (hi & 1) pos = (pos + r) % m;
+        }
+        out[i] = cum + rank + pos;
+    }
+}
+
+void launch_query(const QueryView &q, const void *keys, uint64_t n, uint64_t *out, cudaStream_t st) {
+    if (n == 0) return;
+    uint64_t g = (n + 255) / 256;
+    if (g > 148 * 64) g = 148 * 64;
+    k_query<<<(uint32_t)g, 256, 0, st>>>(q, keys, n, out);
+    note_launches(1);
+}
+
+// Bijection check: every value below n and taken once.
+__global__ void k_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad) {
+    unsigned long long local = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t v = vals[i];
+        if (v >= n) {
+            local++;
+            continue;
+        }
+        uint32_t bit = 1u << (v & 31);
+        if (atomicOr(&bitmap[v >> 5], bit) & bit) local++;
+    }
+    if (local) atomicAdd(bad, local);
+}
+
+void launch_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad,
+                 cudaStream_t st) {
+    if (n == 0) return;
+    uint64_t g = (n + 255) / 256;
+    if (g > 148 * 64) g = 148 * 64;
+    k_mark<<<(uint32_t)g, 256, 0, st>>>(vals, n, bitmap, bad);
+    note_launches(1);
+}
+
+}  // namespace rs

@@ -1,0 +1,25 @@
+// tables.h -- host-side per-node-size tables of libmphf (internal).
+#pragma once
+#include <stdint.h>
+
+namespace rs {
+
+// Tables indexed by node size m in [0, MPHF_MAX_BUCKET] for one (l, rotation):
+//   tau[m]    Golomb-Rice parameter of a node of m keys,
+//   nodes[m]  stored nodes in the subtree of m keys,
+//   fixed[m]  fixed-part bits of that subtree (sum of tau over its nodes).
+struct SizeTables {
+    uint32_t leaf;
+    uint32_t rotation;
+    uint8_t tau[4097];
+    uint32_t nodes[4097];
+    uint32_t fixed[4097];
+};
+
+// Computes (or returns the cached) tables for one leaf size / leaf method.
+const SizeTables &size_tables(uint32_t leaf, uint32_t rotation);
+
+// Golomb-Rice parameter for a node of m keys.
+uint8_t node_tau(uint32_t leaf, uint32_t rotation, uint32_t m);
+
+}  // namespace rs

@@ -1,0 +1,315 @@
+"""Python binding of libmphf (the C ABI in include/mphf.h).
+
+Argument marshalling only: every step of a build or query runs in the CUDA
+library.  PyTorch provides device memory and the current stream.  There is
+no fallback: if the library is missing or cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmphf.so")
+
+OK = 0
+EINVAL = -1
+ENOMEM = -2
+ECUDA = -3
+EDUPLICATE = -4
+ESEARCH_LIMIT = -5
+EBUSY = -6
+EBUCKET = -7
+ENOTIMPL = -8
+ETIMEOUT = -9
+MAX_BUCKET = 4096
+DEFAULT_MAX_VALUE = (1 << 40) - 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MPHFError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = lib().mphf_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = code
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p)]
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_uint32), ("bucket_size", ctypes.c_uint32),
+                ("key_bytes", ctypes.c_uint32), ("rotation_fitting", ctypes.c_uint32),
+                ("max_value", ctypes.c_uint64), ("allocator", ctypes.c_void_p),
+                ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("nb", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
+                ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
+                ("rotation_fitting", ctypes.c_uint32), ("n_nodes", ctypes.c_uint64),
+                ("gr_bits", ctypes.c_uint64), ("gr_words", ctypes.c_uint64),
+                ("ef_words", ctypes.c_uint64), ("ef_low_bits", ctypes.c_uint32 * 2),
+                ("ef_seq_words", ctypes.c_uint64 * 4), ("max_bucket", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_uint64 * 4), ("evals", ctypes.c_uint64 * 4),
+                ("ms_plan", ctypes.c_float), ("ms_search", ctypes.c_float),
+                ("ms_pack", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
+
+class BuildDesc(ctypes.Structure):
+    _fields_ = [("d_keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
+                ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
+                ("rotation_fitting", ctypes.c_uint32), ("max_value", ctypes.c_uint64)]
+
+
+# Every entry point of include/mphf.h: name -> (restype, argtypes)
+_P, _U32, _U64, _I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+SIGNATURES = {
+    "mphf_default_params": (None, [_P]),
+    "mphf_build": (_I, [_P, _U64, _U32, _U32, _P, _P]),
+    "mphf_build_ex": (_I, [_P, _U64, _P, _P, _P]),
+    "mphf_build_host": (_I, [_P, _U64, _P, _P, _P]),
+    "mphf_query": (_I, [_P, _P, _U64, _P, _P]),
+    "mphf_verify": (_I, [_P, _P, _U64, _P, _P]),
+    "mphf_get_info": (_I, [_P, _P]),
+    "mphf_get_values": (_I, [_P, _P, _P, _P, _P]),
+    "mphf_get_bits": (_I, [_P, _P, _P, _P, _P]),
+    "mphf_get_stats": (_I, [_P, _P]),
+    "mphf_tau_table": (_I, [_U32, _U32, _U32, _P]),
+    "mphf_serialize": (_I, [_P, _P, _P, _P]),
+    "mphf_free": (_I, [_P]),
+    "mphf_strerror": (ctypes.c_char_p, [_I]),
+    "mphf_build_batch": (_I, [_P, _U32, _P, _P, _P]),
+    "mphf_kernel_launches": (_U64, []),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libmphf.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2212_09562_b300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise MPHFError(rc, what)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required")
+    return torch
+
+
+def _stream(stream) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+class _DevArray:
+    """Exposes a library-owned device array to torch (no copy)."""
+
+    def __init__(self, ptr: int, count: int, typestr: str = "<u8"):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, count: int):
+    torch = _torch()
+    if count == 0 or not ptr:
+        return torch.zeros(0, dtype=torch.int64, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, count, "<i8"), device="cuda")
+
+
+def key_layout(keys) -> tuple[int, int]:
+    """(n, key_bytes) of a device key tensor: (n,) 64-bit, or (n, 16) bytes / (n, 2) 64-bit."""
+    torch = _torch()
+    if not keys.is_cuda or not keys.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA tensor")
+    if keys.numel() and keys.data_ptr() % 8:
+        raise ValueError("keys must be 8-byte aligned")
+    if keys.dim() == 1 and keys.element_size() == 8:
+        return keys.shape[0], 8
+    if keys.dim() == 2 and keys.dtype == torch.uint8 and keys.shape[1] == 16:
+        return keys.shape[0], 16
+    if keys.dim() == 2 and keys.element_size() == 8 and keys.shape[1] == 2:
+        return keys.shape[0], 16
+    raise ValueError("keys must be (n,) 64-bit or (n, 16) uint8 / (n, 2) 64-bit")
+
+
+def default_params() -> BuildParams:
+    p = BuildParams()
+    lib().mphf_default_params(ctypes.byref(p))
+    return p
+
+
+class MPHF:
+    """A function built on the device by libmphf."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        info = Info()
+        _check(lib().mphf_get_info(self._h, ctypes.byref(info)), "mphf_get_info")
+        self.info = info
+
+    # --- construction -------------------------------------------------------
+    @classmethod
+    def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation: bool = True,
+              max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
+              blocks_per_sm: int = 0, stream=None) -> "MPHF":
+        n, kb = key_layout(keys)
+        p = default_params()
+        p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
+        p.rotation_fitting = 1 if rotation else 0
+        p.max_value = max_value
+        p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_ex(keys.data_ptr() if n else None, n, ctypes.byref(p),
+                                 _stream(stream), ctypes.byref(h))
+        _check(rc, "mphf_build_ex")
+        return cls(h.value)
+
+    @classmethod
+    def build_host(cls, keys: np.ndarray, leaf_size: int = 16, bucket_size: int = 2000,
+                   rotation: bool = True, max_value: int = DEFAULT_MAX_VALUE,
+                   stream=None) -> "MPHF":
+        """Build from keys in host memory (copied to the device inside the call)."""
+        keys = np.ascontiguousarray(keys)
+        kb = 8 if keys.ndim == 1 else 16
+        p = default_params()
+        p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
+        p.rotation_fitting = 1 if rotation else 0
+        p.max_value = max_value
+        h = ctypes.c_void_p()
+        rc = lib().mphf_build_host(keys.ctypes.data if len(keys) else None, len(keys),
+                                   ctypes.byref(p), _stream(stream), ctypes.byref(h))
+        _check(rc, "mphf_build_host")
+        return cls(h.value)
+
+    # --- evaluation ---------------------------------------------------------
+    def query(self, keys, out=None, stream=None):
+        torch = _torch()
+        n, kb = key_layout(keys)
+        if kb != self.info.key_bytes:
+            raise ValueError("key size differs from the built function's")
+        if out is None:
+            out = torch.empty(n, dtype=torch.int64, device=keys.device)
+        _check(lib().mphf_query(self._h, keys.data_ptr() if n else None, n,
+                                out.data_ptr() if n else None, _stream(stream)), "mphf_query")
+        return out
+
+    def verify(self, keys, stream=None) -> int:
+        """Number of keys whose value is out of range or repeated (0 = bijection)."""
+        n, _ = key_layout(keys)
+        bad = ctypes.c_uint64()
+        _check(lib().mphf_verify(self._h, keys.data_ptr() if n else None, n, ctypes.byref(bad),
+                                 _stream(stream)), "mphf_verify")
+        return int(bad.value)
+
+    # --- contents -----------------------------------------------------------
+    def device_arrays(self) -> dict:
+        """Zero-copy torch views (int64) of the library-owned arrays."""
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        _check(lib().mphf_get_values(self._h, *[ctypes.byref(p) for p in ptrs]), "mphf_get_values")
+        gr, ef = ctypes.c_void_p(), ctypes.c_void_p()
+        bits, words = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().mphf_get_bits(self._h, ctypes.byref(gr), ctypes.byref(bits), ctypes.byref(ef),
+                                   ctypes.byref(words)), "mphf_get_bits")
+        nb = self.info.nb
+        return {
+            "values": _device_view(ptrs[0].value, self.info.n_nodes),
+            "node_off": _device_view(ptrs[1].value, nb + 1),
+            "cum_keys": _device_view(ptrs[2].value, nb + 1),
+            "bit_pos": _device_view(ptrs[3].value, nb + 1),
+            "gr": _device_view(gr.value, self.info.gr_words),
+            "ef": _device_view(ef.value, words.value),
+        }
+
+    def host_arrays(self) -> dict:
+        """The same arrays copied to host numpy uint64."""
+        out = {}
+        for k, v in self.device_arrays().items():
+            out[k] = v.cpu().numpy().view(np.uint64).copy()
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().mphf_get_stats(self._h, ctypes.byref(s)), "mphf_get_stats")
+        kinds = ("leaf", "lower1", "lower2", "upper")
+        d = {k: (int(s.trials[i]), int(s.evals[i])) for i, k in enumerate(kinds)}
+        d["ms"] = {"plan": s.ms_plan, "search": s.ms_search, "pack": s.ms_pack, "total": s.ms_total}
+        return d
+
+    def serialize(self, stream=None) -> bytes:
+        n = ctypes.c_size_t()
+        _check(lib().mphf_serialize(self._h, None, ctypes.byref(n), _stream(stream)), "mphf_serialize")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().mphf_serialize(self._h, buf, ctypes.byref(n), _stream(stream)), "mphf_serialize")
+        return buf.raw[: n.value]
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().mphf_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().mphf_kernel_launches())
+
+
+def tau_table(leaf_size: int, rotation: bool, max_m: int = MAX_BUCKET) -> np.ndarray:
+    out = np.zeros(max_m + 1, np.uint8)
+    _check(lib().mphf_tau_table(leaf_size, 1 if rotation else 0, max_m, out.ctypes.data),
+           "mphf_tau_table")
+    return out
+
+
+def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation: bool = True,
+                max_value: int = 0, stream=None) -> list[MPHF]:
+    """Many independent builds in one call (see mphf_build_batch)."""
+    count = len(keys_list)
+    descs = (BuildDesc * max(count, 1))()
+    for i, (k, l) in enumerate(zip(keys_list, leaf_sizes)):
+        n, kb = key_layout(k)
+        descs[i] = BuildDesc(k.data_ptr() if n else None, n, l, bucket_size, kb,
+                             1 if rotation else 0, max_value)
+    outs = (ctypes.c_void_p * max(count, 1))()
+    sts = (ctypes.c_int * max(count, 1))()
+    rc = lib().mphf_build_batch(descs, count, _stream(stream), outs, sts)
+    if rc != OK:
+        for i in range(count):
+            if outs[i]:
+                lib().mphf_free(ctypes.c_void_p(outs[i]))
+        _check(rc, "mphf_build_batch")
+    return [MPHF(outs[i]) for i in range(count)]

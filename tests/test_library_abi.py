@@ -1,0 +1,71 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/mphf.h declares, and its host-side tables equal the oracle's.
+
+The Golomb-Rice parameter per node size (Section 2.2, "Representation") is
+computed independently by the library and by the oracle; parity of the
+packed bits needs the two tables to be equal.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2212_09562_b300 import build as B
+from paper_2212_09562_b300 import mphf as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return M.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "mphf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mphf_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_surface():
+    names = declared_functions()
+    assert set(names) == set(M.SIGNATURES), set(names) ^ set(M.SIGNATURES)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_error_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9):
+        assert lib.mphf_strerror(code)
+    assert lib.mphf_strerror(-4).decode().startswith("duplicate")
+
+
+def test_default_params(lib):
+    p = M.default_params()
+    assert (p.leaf_size, p.bucket_size, p.key_bytes, p.rotation_fitting) == (16, 2000, 8, 1)
+    assert p.max_value == M.DEFAULT_MAX_VALUE
+
+
+def test_invalid_arguments_are_rejected_without_a_device(lib):
+    h = ctypes.c_void_p()
+    p = M.default_params()
+    for field, value in [("leaf_size", 1), ("leaf_size", 25), ("bucket_size", 0),
+                         ("bucket_size", 3001), ("key_bytes", 4), ("threads_per_block", 100)]:
+        q = M.default_params()
+        setattr(q, field, value)
+        assert lib.mphf_build_ex(None, 0, ctypes.byref(q), None, ctypes.byref(h)) == M.EINVAL
+    assert lib.mphf_build_ex(None, 5, ctypes.byref(p), None, ctypes.byref(h)) == M.EINVAL
+    assert lib.mphf_query(None, None, 0, None, None) == M.EINVAL
+    assert lib.mphf_tau_table(1, 1, 10, None) == M.EINVAL
+
+
+@pytest.mark.parametrize("leaf", [2, 3, 5, 7, 8, 10, 12, 16, 20, 24])
+@pytest.mark.parametrize("rotation", [False, True])
+def test_tau_tables_equal_the_oracle(lib, orc, leaf, rotation):
+    assert np.array_equal(M.tau_table(leaf, rotation), orc.tau_table(leaf, rotation))
