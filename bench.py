@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override the key count (profiling runs)")
     return ap.parse_args()
 
 
@@ -136,7 +137,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    w = W.WORKLOADS[args.workload]
+    w = workload(args)
     keys = W.keys_for(w)
     for _ in range(max(0, min(args.warmup, 1))):
         cpu_baseline(w, keys, 2.0)
@@ -158,6 +159,13 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def workload(args):
+    w = W.WORKLOADS[args.workload]
+    if args.n:
+        w = W.Workload(w.name + f"_n{args.n}", args.n, w.leaf, w.bucket, w.key_bytes, w.rotation, w.seed)
+    return w
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -167,7 +175,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2212_09562_b300 import mphf as M
     M.lib()
-    w = W.WORKLOADS[args.workload]
+    w = workload(args)
     keys = W.random_keys(w.n, w.key_bytes, w.seed + rank) if rank else W.keys_for(w)
     dkeys = torch.from_numpy(keys.view(np.int64) if keys.ndim == 1 else keys).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
