@@ -25,6 +25,10 @@
 
 using namespace rs;
 
+#ifndef MPHF_LPT
+#define MPHF_LPT 1
+#endif
+
 namespace {
 
 struct DevTables {
@@ -211,6 +215,8 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, vo
     InstDesc *d_inst = nullptr;
     WorkItem *items = nullptr;
     uint64_t *host_small = nullptr;
+    uint64_t *size_hist = nullptr;
+    uint32_t *size_cursor = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     for (auto &e : ev) cudaEventCreate(&e);
     cudaEventRecord(ev[0], st);
@@ -242,6 +248,10 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, vo
         CK(lo_s = (uint64_t *)mem.get(n * 8));
         CK(bb_s = (uint8_t *)mem.get(n));
         CK(counters = (uint64_t *)mem.get(8 * 8));
+        CK(size_hist = (uint64_t *)mem.get(4098 * 8));
+        CK(size_cursor = (uint32_t *)mem.get(4097 * 4));
+        CU(cudaMemsetAsync(size_hist, 0, 4098 * 8, st));
+        CU(cudaMemsetAsync(size_cursor, 0, 4097 * 4, st));
         CU(cudaMallocHost(&host_small, 64));
         CU(cudaMemsetAsync(h->cum_keys, 0, (nb + 1) * 8, st));
         CU(cudaMemsetAsync(h->node_off, 0, (nb + 1) * 8, st));
@@ -251,9 +261,10 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, vo
 
         // fingerprints, bucket sizes, plan, offsets
         launch_fp_hist(d_keys, n, p->key_bytes, nb, h->cum_keys, st);
-        launch_plan(h->cum_keys, nb, h->tabs.nodes, node_cnt, small, small + 1, st);
+        launch_plan(h->cum_keys, nb, h->tabs.nodes, node_cnt, small, small + 1, size_hist, st);
         launch_exclusive_scan(h->cum_keys, nb + 1, scan_tmp, st);
         launch_exclusive_scan(node_cnt, nb + 1, scan_tmp, st);
+        launch_exclusive_scan(size_hist, 4098, scan_tmp, st);
         CU(cudaGetLastError());
         CU(cudaMemcpyAsync(host_small, node_cnt + nb, 8, cudaMemcpyDeviceToHost, st));
         CU(cudaMemcpyAsync(host_small + 1, small, 8, cudaMemcpyDeviceToHost, st));
@@ -288,11 +299,23 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, vo
             hd.leaf = leaf;
             hd.rotation = rot;
             hd.nb = (uint32_t)nb;
-            hd.pad = 0;
+            hd.k30 = 1u << 2;
+            hd.k27 = 1u << 5;
+            hd.k31 = 1u << 1;
+            {
+                Shape shp = make_shape(leaf);
+                hd.red[0] = (uint32_t)((1ull << 32) % leaf);
+                hd.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
+                hd.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
+            }
             CU(cudaMemcpyAsync(d_inst, &hd, sizeof(hd), cudaMemcpyHostToDevice, st));
+#if MPHF_LPT
+            launch_items_by_size(h->cum_keys, nb, size_hist, size_cursor, items, 0, st);
+#else
             k_items<<<(uint32_t)((nb + 255) / 256 < 4096 ? (nb + 255) / 256 : 4096), 256, 0, st>>>(
                 items, (uint32_t)nb, 0);
             note_launches(1);
+#endif
             SearchLaunch L = plan_search_launch(max_m, (uint32_t)nb, p->threads_per_block,
                                                 p->blocks_per_sm);
             cudaEventRecord(ev[2], st);
@@ -373,6 +396,8 @@ done:
     mem.put(node_m);
     mem.put(items);
     mem.put(d_inst);
+    mem.put(size_hist);
+    mem.put(size_cursor);
     if (host_small) {
         cudaStreamSynchronize(st);
         cudaFreeHost(host_small);

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "engine.h"
 
@@ -65,9 +67,11 @@ void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 }
 
 // ---------------------------------------------------------------------------
-// Plan: nodes per bucket, oversized buckets, largest bucket.
+// Plan: nodes per bucket, oversized buckets, largest bucket, and a histogram
+// of bucket sizes in descending order (size_hist[4096 - m]) for the work order.
 __global__ void k_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab,
-                       uint64_t *node_cnt, uint32_t *status, uint32_t *max_m) {
+                       uint64_t *node_cnt, uint32_t *status, uint32_t *max_m,
+                       unsigned long long *size_hist) {
     for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nb;
          b += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t m = counts[b];
@@ -76,15 +80,38 @@ __global__ void k_plan(const uint64_t *counts, uint64_t nb, const uint32_t *node
             node_cnt[b] = 0;
         } else {
             node_cnt[b] = nodes_tab[m];
+            if (size_hist) atomicAdd(&size_hist[4096 - m], 1ull);
         }
         atomicMax(max_m, (uint32_t)(m > 0xFFFFFFFFull ? 0xFFFFFFFFull : m));
     }
 }
 
 void launch_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab, uint64_t *node_cnt,
-                 uint32_t *status, uint32_t *max_m, cudaStream_t st) {
+                 uint32_t *status, uint32_t *max_m, uint64_t *size_hist, cudaStream_t st) {
     if (nb == 0) return;
-    k_plan<<<grid_for(nb, 256), 256, 0, st>>>(counts, nb, nodes_tab, node_cnt, status, max_m);
+    k_plan<<<grid_for(nb, 256), 256, 0, st>>>(counts, nb, nodes_tab, node_cnt, status, max_m,
+                                               (unsigned long long *)size_hist);
+    note_launches(1);
+}
+
+// Work order: buckets by decreasing size (longest first), from the scanned
+// descending size histogram; the order among equal sizes is arbitrary.
+__global__ void k_items_by_size(const uint64_t *bucket_off, uint64_t nb, const uint64_t *size_off,
+                                uint32_t *size_cursor, WorkItem *items, uint32_t inst) {
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nb;
+         b += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t m = bucket_off[b + 1] - bucket_off[b];
+        uint32_t k = m > 4096 ? 0 : 4096 - (uint32_t)m;
+        uint64_t pos = size_off[k] + atomicAdd(&size_cursor[k], 1u);
+        items[pos] = WorkItem{inst, (uint32_t)b};
+    }
+}
+
+void launch_items_by_size(const uint64_t *bucket_off, uint64_t nb, const uint64_t *size_off,
+                          uint32_t *size_cursor, WorkItem *items, uint32_t inst, cudaStream_t st) {
+    if (nb == 0) return;
+    k_items_by_size<<<grid_for(nb, 256), 256, 0, st>>>(bucket_off, nb, size_off, size_cursor, items,
+                                                        inst);
     note_launches(1);
 }
 
@@ -208,6 +235,8 @@ struct BlockState {
     uint32_t nleaves, leaf_next, flags, item;
     unsigned long long found;
     uint32_t cnt[16];
+    unsigned long long lut64[16];  // child -> counter increment (last child: 0)
+    uint32_t lut32[16];
 };
 
 struct SmemArrays {
@@ -217,8 +246,18 @@ struct SmemArrays {
     uint8_t *leaf_m;
 };
 
-// Number of bits of x (x >= 1): the packed-counter field width for parts <= x.
+// Number of bits of x (x >= 1).
 __host__ __device__ constexpr uint32_t bit_width_ce(uint32_t x) { return x ? 1 + bit_width_ce(x >> 1) : 0; }
+
+// Width of a packed child counter field for parts of at most `unit` keys:
+// the smallest w with 2^w >= unit + 2 (see search_lower for why).
+__host__ __device__ constexpr uint32_t field_width(uint32_t unit) { return bit_width_ce(unit + 1); }
+
+// A node of m keys with np parts has its counter fit 32 bits when the top
+// counted field (np - 2) cannot push past bit 31 even with all m keys in it.
+__host__ __device__ constexpr bool counter_fits32(uint32_t m, uint32_t w, uint32_t np) {
+    return ((uint64_t)m << (w * (np - 2))) < (1ull << 32);
+}
 
 template <uint32_t U>
 struct DivCT {
@@ -229,29 +268,154 @@ struct DivRT {
     __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return div_unit(p, magic); }
 };
 
-// Lower aggregation split: all threads of the block test consecutive seeds;
-// counts are packed w-bit fields, one per child, compared with the target word.
+// ---------------------------------------------------------------------------
+// The node hash mix64(x + s) on 32-bit halves.  The search is bound by the
+// integer ALU pipe, so the 32-bit pieces of the 64-bit xor-shifts
+// z ^= z >> k (lo >> k, hi << (32 - k), hi >> k) are computed as products
+// with the runtime constant 2^(32 - k) on the multiply pipe, which would
+// otherwise idle; only the xors stay on the ALU pipe.  MPHF_EVAL selects
+// the instruction mix (0: plain 64-bit C; 1: wide multiply for the high
+// word; 2: three 32-bit multiplies; 3: like 2 for the last xor-shift too).
+#ifndef MPHF_EVAL
+#define MPHF_EVAL 0
+#endif
+#ifndef MPHF_RTC
+#define MPHF_RTC 1
+#endif
+#ifndef MPHF_SPT
+#define MPHF_SPT 1
+#endif
+
+__device__ __forceinline__ void xorshift_mul(uint32_t &zl, uint32_t &zh, uint32_t k) {
+    uint32_t a, b, c;
+#if MPHF_EVAL == 1
+    uint64_t w;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(w) : "r"(zh), "r"(k));
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(a) : "r"(zl), "r"(k));
+    b = (uint32_t)w;
+    c = (uint32_t)(w >> 32);
+#else
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(a) : "r"(zl), "r"(k));  // lo >> s
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(b) : "r"(zh), "r"(k));  // hi << (32 - s)
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(c) : "r"(zh), "r"(k));  // hi >> s
+#endif
+    zl ^= a | b;
+    zh ^= c;
+}
+
+__device__ __forceinline__ void mul64_const(uint32_t &zl, uint32_t &zh, uint32_t cl, uint32_t ch) {
+    uint64_t w = (uint64_t)zl * cl;
+    uint32_t nh = (uint32_t)(w >> 32) + zl * ch + zh * cl;
+    zl = (uint32_t)w;
+    zh = nh;
+}
+
+struct Mixer {
+    uint32_t k30, k27, k31;  // 2^2, 2^5, 2^1, held in registers (kernel arguments)
+    __device__ __forceinline__ void operator()(uint64_t z, uint32_t &hl, uint32_t &hh) const {
+#if MPHF_EVAL == 0
+        uint64_t h = mix64(z);
+        hl = (uint32_t)h;
+        hh = (uint32_t)(h >> 32);
+#else
+        uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+        xorshift_mul(zl, zh, k30);
+        mul64_const(zl, zh, 0x1CE4E5B9u, 0xBF58476Du);
+        xorshift_mul(zl, zh, k27);
+        mul64_const(zl, zh, 0x133111EBu, 0x94D049BBu);
+#if MPHF_EVAL == 3
+        xorshift_mul(zl, zh, k31);
+        hl = zl;
+        hh = zh;
+#else
+        hl = zl ^ ((zl >> 31) | (zh << 1));
+        hh = zh ^ (zh >> 31);
+#endif
+#endif
+    }
+};
+
+// h mod m from the halves of h (same reduction as ModRT / ModCT).
+__device__ __forceinline__ uint32_t mod_halves(const ModRT &r, uint32_t hl, uint32_t hh) {
+    uint64_t t = (uint64_t)hh * r.c + hl;
+    uint64_t u = (uint64_t)(uint32_t)(t >> 32) * r.c + (uint32_t)t;
+    uint32_t v = (uint32_t)(u >> 32) * r.c + (uint32_t)u;
+    return (uint32_t)__umul64hi(r.M * v, r.m);
+}
+// Compile-time modulus with the reduction constant c = 2^32 mod MM held in a
+// register: for the benchmark node sizes c is a power of two (32 for 112,
+// 256 for 560), and as an immediate the compiler turns the wide multiply-adds
+// into 64-bit shift/add chains on the integer ALU pipe, the pipe the search
+// is bound by.  The last step v mod MM keeps the constant divisor.
+template <uint32_t MM>
+struct ModCTR {
+    uint32_t c;
+};
+template <uint32_t MM>
+__device__ __forceinline__ uint32_t mod_halves(const ModCTR<MM> &r, uint32_t hl, uint32_t hh) {
+    if constexpr ((MM & (MM - 1)) == 0) {
+        return hl & (MM - 1);
+    } else {
+#if MPHF_RTC
+        const uint32_t c = r.c;
+#else
+        constexpr uint32_t c = (uint32_t)((1ull << 32) % MM);
+#endif
+        uint64_t t = (uint64_t)hh * c + hl;
+        uint64_t u = (uint64_t)(uint32_t)(t >> 32) * c + (uint32_t)t;
+        uint32_t v = (uint32_t)(u >> 32) * c + (uint32_t)u;
+        return v % MM;
+    }
+}
+// The constant comes from the instance descriptor in device memory, so the
+// compiler cannot fold it back into an immediate.
+template <uint32_t MM>
+__device__ __forceinline__ ModCTR<MM> make_modct(uint32_t c_from_memory) {
+    return ModCTR<MM>{c_from_memory};
+}
+
+// Lower aggregation split: all threads of the block test consecutive seeds.
+// Each thread counts the keys of every child but the last in w-bit fields of
+// one word (the increment of child c is lut[c] = 2^(w c), the last child's is
+// 0: its count is m minus the others).  The seed is valid iff the word equals
+// sum_{c < np-1} p_c 2^(w c).  No wrong count can match: as long as no field
+// carries past the word (counter_fits32 / 64-bit words), equal words mean the
+// normalised digits of the counts equal the p_c, each carry lowers the digit
+// sum by 2^w - 1, so any carry would need the last child to hold p_last -
+// (2^w - 1) < 0 keys (p_last <= unit <= 2^w - 2).
 // The whole chunk of seeds is decided before the next one starts, so the
 // smallest working seed wins.
-template <class Mod, class Div>
-__device__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div, uint32_t w,
-                                 uint64_t expected, uint64_t maxv, bool &limit, BlockState &S) {
+template <class Cnt, class Mod, class Div>
+__device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div, const Cnt *lut,
+                                 Cnt expected, const Mixer &mx, uint64_t maxv, bool &limit,
+                                 BlockState &S) {
     const uint32_t T = blockDim.x;
-    for (uint64_t base = 0;; base += T) {
-        uint64_t s = base + threadIdx.x;
-        uint64_t cnt = 0;
+    for (uint64_t base = 0;; base += (uint64_t)T * MPHF_SPT) {
+        Cnt cnt[MPHF_SPT];
+#pragma unroll
+        for (int j = 0; j < MPHF_SPT; j++) cnt[j] = 0;
+        const uint64_t s0 = base + threadIdx.x;
 #pragma unroll 4
         for (uint32_t i = 0; i < m; i++) {
-            uint32_t p = mod(mix64(xs[i] + s));
-            cnt += 1ull << (w * div(p));
+            const uint64_t x = xs[i];
+#pragma unroll
+            for (int j = 0; j < MPHF_SPT; j++) {
+                uint32_t hl, hh;
+                mx(x + s0 + (uint64_t)j * T, hl, hh);
+                cnt[j] += lut[div(mod_halves(mod, hl, hh))];
+            }
         }
-        bool ok = cnt == expected && s <= maxv;
+        uint64_t best = ~0ull;
+#pragma unroll
+        for (int j = MPHF_SPT - 1; j >= 0; j--)
+            if (cnt[j] == expected && s0 + (uint64_t)j * T <= maxv) best = s0 + (uint64_t)j * T;
+        const bool ok = best != ~0ull;
         if (__syncthreads_or(ok)) {
-            if (ok) atomicMin(&S.found, (unsigned long long)s);
+            if (ok) atomicMin(&S.found, (unsigned long long)best);
             __syncthreads();
             return S.found;
         }
-        if (base + T > maxv) {
+        if (base + (uint64_t)T * MPHF_SPT > maxv) {
             limit = true;
             return 0;
         }
@@ -260,14 +424,18 @@ __device__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div di
 
 // Fanout-2 split: one counter of keys hashed below `left`.
 template <class Mod>
-__device__ uint64_t search_upper(const uint64_t *xs, uint32_t m, Mod mod, uint32_t left,
-                                 uint64_t maxv, bool &limit, BlockState &S) {
+__device__ __forceinline__ uint64_t search_upper(const uint64_t *xs, uint32_t m, Mod mod, uint32_t left,
+                                 const Mixer &mx, uint64_t maxv, bool &limit, BlockState &S) {
     const uint32_t T = blockDim.x;
     for (uint64_t base = 0;; base += T) {
         uint64_t s = base + threadIdx.x;
         uint32_t cnt = 0;
 #pragma unroll 4
-        for (uint32_t i = 0; i < m; i++) cnt += mod(mix64(xs[i] + s)) < left;
+        for (uint32_t i = 0; i < m; i++) {
+            uint32_t hl, hh;
+            mx(xs[i] + s, hl, hh);
+            cnt += mod_halves(mod, hl, hh) < left;
+        }
         bool ok = cnt == left && s <= maxv;
         if (__syncthreads_or(ok)) {
             if (ok) atomicMin(&S.found, (unsigned long long)s);
@@ -283,13 +451,17 @@ __device__ uint64_t search_upper(const uint64_t *xs, uint32_t m, Mod mod, uint32
 
 // Leaf, plain brute force (Section 2.2 "Bijections"): one warp, lane = seed.
 template <class Mod>
-__device__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, Mod mod, uint64_t maxv, bool &limit,
-                               uint32_t lane) {
+__device__ __forceinline__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, Mod mod, const Mixer &mx,
+                               uint64_t maxv, bool &limit, uint32_t lane) {
     const uint32_t full = (1u << m) - 1;
     for (uint64_t s0 = 0;; s0 += 32) {
         uint64_t s = s0 + lane;
         uint32_t mask = 0;
-        for (uint32_t i = 0; i < m; i++) mask |= 1u << mod(mix64(xs[i] + s));
+        for (uint32_t i = 0; i < m; i++) {
+            uint32_t hl, hh;
+            mx(xs[i] + s, hl, hh);
+            mask |= 1u << mod_halves(mod, hl, hh);
+        }
         uint32_t ball = __ballot_sync(0xffffffffu, mask == full);
         if (ball) {
             uint64_t x = s0 + (uint32_t)(__ffs(ball) - 1);
@@ -307,8 +479,8 @@ __device__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, Mod mod, uint64_t
 // bits of a, keys of B bits of b; the smallest r with a | rot_m^r(b) full.
 // The lowest lane with a hit has the smallest k, hence the smallest k*m + r.
 template <class Mod>
-__device__ uint64_t leaf_rotation(const uint64_t *xs, const uint8_t *bbs, uint32_t m, Mod mod,
-                                  uint64_t maxv, bool &limit, uint32_t lane) {
+__device__ __forceinline__ uint64_t leaf_rotation(const uint64_t *xs, const uint8_t *bbs, uint32_t m, Mod mod,
+                                  const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
     const uint32_t full = (1u << m) - 1;
     uint32_t nb = 0;
     for (uint32_t i = 0; i < m; i++) nb += bbs[i];
@@ -317,7 +489,9 @@ __device__ uint64_t leaf_rotation(const uint64_t *xs, const uint8_t *bbs, uint32
         uint64_t s = (k0 + lane) * m;
         uint32_t a = 0, b = 0;
         for (uint32_t i = 0; i < m; i++) {
-            uint32_t bit = 1u << mod(mix64(xs[i] + s));
+            uint32_t hl, hh;
+            mx(xs[i] + s, hl, hh);
+            uint32_t bit = 1u << mod_halves(mod, hl, hh);
             if (bbs[i])
                 b |= bit;
             else
@@ -347,7 +521,7 @@ __device__ uint64_t leaf_rotation(const uint64_t *xs, const uint8_t *bbs, uint32
 }
 
 // Any two equal lo words among keys [0, m) of the block's bucket.
-__device__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
+__device__ __forceinline__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
     bool dup = false;
     for (uint32_t i = threadIdx.x; i < m && !dup; i += blockDim.x)
         for (uint32_t j = i + 1; j < m; j++)
@@ -359,7 +533,7 @@ __device__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
 }
 
 template <int LEAF>
-__device__ void split_node(const InstDesc &d, const Shape &sh, uint32_t off, uint32_t m,
+__device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, uint32_t off, uint32_t m,
                            uint32_t depth, uint32_t pidx, uint64_t nbase, uint32_t bucket_m,
                            const SmemArrays &A, BlockState &S) {
     const uint32_t T = blockDim.x, tid = threadIdx.x;
@@ -373,32 +547,50 @@ __device__ void split_node(const InstDesc &d, const Shape &sh, uint32_t off, uin
     uint64_t x = 0;
     bool limit = false;
     const ModRT mrt = make_mod(m);
+    const Mixer mx{d.k30, d.k27, d.k31};
     if (kind == NODE_UPPER) {
-        x = search_upper(xs, m, mrt, upper_left(sh, m), d.max_value, limit, S);
+        x = search_upper(xs, m, mrt, upper_left(sh, m), mx, d.max_value, limit, S);
     } else {
         const uint32_t unit = lower_unit(sh, m);
-        const uint32_t w = counter_width(unit);
+        const uint32_t w = field_width(unit);
         uint64_t expected = 0;
-        for (uint32_t c = 0; c < np; c++) expected += (uint64_t)part_size(sh, m, c) << (w * c);
+        for (uint32_t c = 0; c + 1 < np; c++) expected += (uint64_t)part_size(sh, m, c) << (w * c);
+        if (tid < 16) {
+            uint64_t inc = tid + 1 < np ? 1ull << (w * tid) : 0;
+            S.lut64[tid] = inc;
+            S.lut32[tid] = (uint32_t)inc;
+        }
+        __syncthreads();
+        bool done = false;
         if constexpr (LEAF != 0) {
-            // full lower-1 and lower-2 nodes: compile-time modulus, unit and field width
+            // full lower-1 and lower-2 nodes: compile-time modulus, unit, counter width
             constexpr uint32_t f1 = ((35u * LEAF + 154u) / 100u) < 2 ? 2 : (35u * LEAF + 154u) / 100u;
             constexpr uint32_t f2 = ((21u * LEAF + 189u) / 100u) < 2 ? 2 : (21u * LEAF + 189u) / 100u;
             constexpr uint32_t L1 = f1 * LEAF, L2 = f2 * L1;
-            constexpr uint32_t W1 = bit_width_ce(LEAF), W2 = bit_width_ce(L1);
+            constexpr bool n1 = counter_fits32(L1, field_width(LEAF), f1);
+            constexpr bool n2 = counter_fits32(L2, field_width(L1), f2);
+            using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
+            using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
             if (m == L1) {
-                x = search_lower(xs, m, ModCT<L1>(), DivCT<LEAF>(), W1, expected, d.max_value,
-                                 limit, S);
+                const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
+                x = search_lower<C1>(xs, m, make_modct<L1>(d.red[1]), DivCT<LEAF>(), lut, (C1)expected, mx,
+                                     d.max_value, limit, S);
+                done = true;
             } else if (m == L2) {
-                x = search_lower(xs, m, ModCT<L2>(), DivCT<L1>(), W2, expected, d.max_value,
-                                 limit, S);
-            } else {
-                x = search_lower(xs, m, mrt, DivRT{unit_magic(unit)}, w, expected, d.max_value,
-                                 limit, S);
+                const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
+                x = search_lower<C2>(xs, m, make_modct<L2>(d.red[2]), DivCT<L1>(), lut, (C2)expected, mx,
+                                     d.max_value, limit, S);
+                done = true;
             }
-        } else {
-            x = search_lower(xs, m, mrt, DivRT{unit_magic(unit)}, w, expected, d.max_value, limit,
-                             S);
+        }
+        if (!done) {
+            const DivRT dv{unit_magic(unit)};
+            if (counter_fits32(m, w, np))
+                x = search_lower<uint32_t>(xs, m, mrt, dv, S.lut32, (uint32_t)expected, mx,
+                                           d.max_value, limit, S);
+            else
+                x = search_lower<unsigned long long>(xs, m, mrt, dv, S.lut64, expected, mx,
+                                                     d.max_value, limit, S);
         }
     }
     if (limit) {  // uniform: decided after a block-wide vote
@@ -454,9 +646,10 @@ __device__ void split_node(const InstDesc &d, const Shape &sh, uint32_t off, uin
 }
 
 template <int LEAF>
-__device__ void leaf_phase(const InstDesc &d, uint64_t nbase, const SmemArrays &A, BlockState &S) {
+__device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, const SmemArrays &A, BlockState &S) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t salt = level_salt(0);
+    const Mixer mx{d.k30, d.k27, d.k31};
     for (;;) {
         uint32_t j = 0;
         if (lane == 0) j = atomicAdd(&S.leaf_next, 1u);
@@ -479,14 +672,14 @@ __device__ void leaf_phase(const InstDesc &d, uint64_t nbase, const SmemArrays &
         bool done = false;
         if constexpr (LEAF != 0) {
             if (m == (uint32_t)LEAF) {  // full leaf: compile-time modulus
-                x = d.rotation ? leaf_rotation(xs, A.bb + off, m, ModCT<LEAF>(), d.max_value, limit, lane)
-                               : leaf_plain(xs, m, ModCT<LEAF>(), d.max_value, limit, lane);
+                x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
+                               : leaf_plain(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
                 done = true;
             }
         }
         if (!done)
-            x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_mod(m), d.max_value, limit, lane)
-                           : leaf_plain(xs, m, make_mod(m), d.max_value, limit, lane);
+            x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane)
+                           : leaf_plain(xs, m, make_mod(m), mx, d.max_value, limit, lane);
         if (lane == 0) {
             if (limit) {
                 atomicOr(&S.flags, ST_LIMIT);
@@ -499,7 +692,7 @@ __device__ void leaf_phase(const InstDesc &d, uint64_t nbase, const SmemArrays &
 }
 
 template <int LEAF>
-__device__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
+__device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
                                BlockState &S) {
     const uint32_t tid = threadIdx.x, T = blockDim.x;
     const Shape sh = make_shape(LEAF ? (uint32_t)LEAF : d.leaf);
@@ -593,7 +786,7 @@ SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads
                                 uint32_t blocks_per_sm) {
     SearchLaunch L;
     L.cap = max_m < 2 ? 2 : max_m;
-    L.threads = threads ? threads : 256;
+    L.threads = threads ? threads : 512;
     L.smem_bytes = search_smem(L.cap);
     int dev = 0, sms = 148, occ = 1;
     cudaGetDevice(&dev);

@@ -21,7 +21,9 @@ struct InstDesc {
     uint32_t *status;            // ST_* bits
     uint64_t max_value;
     uint32_t leaf, rotation;
-    uint32_t nb, pad;
+    uint32_t nb;
+    uint32_t k30, k27, k31;      // 4, 32, 2: multipliers of the hash's xor-shifts
+    uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
 };
 
 // One unit of work: a bucket of an instance.
@@ -44,7 +46,12 @@ uint64_t launches_total();
 void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint64_t *counts,
                     cudaStream_t st);
 void launch_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab, uint64_t *node_cnt,
-                 uint32_t *status, uint32_t *max_m, cudaStream_t st);
+                 uint32_t *status, uint32_t *max_m, uint64_t *size_hist, cudaStream_t st);
+// Work items of one instance ordered by decreasing bucket size; size_off is
+// the exclusive scan of the size histogram (4097 + 1 entries), size_cursor
+// 4097 zeroed counters.
+void launch_items_by_size(const uint64_t *bucket_off, uint64_t nb, const uint64_t *size_off,
+                          uint32_t *size_cursor, WorkItem *items, uint32_t inst, cudaStream_t st);
 // Exclusive scan of n + 1 values in place (the last input should be 0; the
 // last output is then the total).  tmp needs scan_tmp_words(n + 1) words.
 uint64_t scan_tmp_words(uint64_t len);

@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmphf.so")
+# MPHF_LIBRARY selects another build of the same library (e.g. a tuning variant).
+LIB_PATH = os.environ.get("MPHF_LIBRARY") or os.path.join(HERE, "libmphf.so")
 
 OK = 0
 EINVAL = -1
