@@ -64,7 +64,7 @@ typedef struct {
  *   leaf_size        l, 2..24 (Section 2.2: leaves of l keys).
  *   bucket_size      b, 1..3000; nb = ceil(n / b) buckets.
  *   key_bytes        8 or 16.
- *   rotation_fitting 1: leaves use rotation fitting (Section 3); 0: plain
+ *   rotation_fitting 1: leaves use rotation fitting (Section 4); 0: plain
  *                    brute force (Section 2.2, "Bijections").
  *   max_value        largest value any node may store; a node that needs
  *                    more fails the build with MPHF_ESEARCH_LIMIT.
@@ -128,7 +128,7 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *param
 int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *params,
                     void *stream, mphf_t **out);
 
-/* Evaluates h on n keys (Section 2.2, "Query"; Section 3 for the rotation
+/* Evaluates h on n keys (Section 2.2, "Query"; Section 4 for the rotation
  * of the keys in B).  d_out[i] = h(key i) in [0, n_built) for keys of the
  * built set.  Asynchronous on the stream. */
 int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out, void *stream);

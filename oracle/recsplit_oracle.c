@@ -27,7 +27,7 @@
  *       moves bit p of B's mask to bit (p + r) mod m.
  *   R6  Golomb-Rice parameter per node from Kiely's rule for a geometric
  *       source; the success probability of a rotation leaf uses the bound of
- *       the appendix lemma.
+ *       the Appendix A lemma.
  *
  * Parity pins: see the oracle test files (fixed points from the paper's
  * figures, closed forms, invariants, brute force on tiny inputs).  The
@@ -58,7 +58,7 @@ enum { ST_LEAF = 0, ST_LOWER1 = 1, ST_LOWER2 = 2, ST_UPPER = 3, ST_N = 4 };
 /* ------------------------------------------------------------------------ */
 /* R1: hashing.  SplitMix64 output function (Steele, Lea, Flood, OOPSLA     */
 /* 2014).  The paper's initial hash (Section 2.2, "Splitting Trees"; master */
-/* hash codes in Section 5) is only required to be of high quality.        */
+/* hash codes in Section 6) is only required to be of high quality.        */
 /* ------------------------------------------------------------------------ */
 uint64_t orc_mix64(uint64_t z) {
     z ^= z >> 30;
@@ -206,7 +206,7 @@ typedef struct {
 } orc_stats;
 
 /* ------------------------------------------------------------------------ */
-/* Split search (Section 2.2 "Splitting Trees"; Section 4.1 "Splittings"):  */
+/* Split search (Section 2.2 "Splitting Trees"; Section 5.1 "Splittings"):  */
 /* the smallest s >= 0 whose hash gives every child exactly its part size.  */
 /* ------------------------------------------------------------------------ */
 static int split_search(const orc_shape *sh, const uint64_t *lo, uint32_t m, uint32_t depth,
@@ -263,11 +263,11 @@ static uint32_t rotl_m(uint32_t x, uint32_t r, uint32_t m) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Leaf bijection with rotation fitting (Section 3).  Only seeds k*m are    */
+/* Leaf bijection with rotation fitting (Section 4).  Only seeds k*m are    */
 /* hashed; the keys of A set bits of a, the keys of B bits of b.  The first */
 /* k for which some rotation r makes a | rot(b, r) full is taken, with the  */
 /* smallest such r, and k*m + r is stored (the smallest stored number, as   */
-/* Section 4.1 requires).                                                   */
+/* Section 5.1 requires).                                                   */
 /* ------------------------------------------------------------------------ */
 static int leaf_rotation(const uint64_t *lo, const uint64_t *hi, uint32_t m, uint64_t max_value,
                          uint64_t *out, orc_stats *st) {
@@ -524,7 +524,7 @@ static int build_node(bucket_ctx *cx, uint64_t *lo, uint64_t *hi, uint64_t *tlo,
     rc = split_search(sh, lo, m, depth, cx->max_value, &x, cx->st);
     if (rc) return rc;
     cx->values[cx->count++] = x;
-    /* regroup the keys by child with the seed found (Section 4.1, end of
+    /* regroup the keys by child with the seed found (Section 5.1, end of
      * "Splittings"): counting sort by child index */
     uint32_t parts[ORC_MAX_PARTS], start[ORC_MAX_PARTS];
     uint32_t np = parts_of(sh, m, parts);
@@ -607,7 +607,7 @@ static void free_grouped(grouped *g) {
     free(g->cum);
 }
 
-/* Section 4.2: every thread takes a consecutive range of buckets. */
+/* Section 5.2: every thread takes a consecutive range of buckets. */
 typedef struct {
     const grouped *g;
     const orc_shape *sh;
@@ -889,7 +889,7 @@ int orc_build_sample(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32
 }
 
 /* ------------------------------------------------------------------------ */
-/* Query (Section 2.2 "Query"; Section 3: a rotation is an addition mod m   */
+/* Query (Section 2.2 "Query"; Section 4: a rotation is an addition mod m   */
 /* for the keys of B).                                                      */
 /* ------------------------------------------------------------------------ */
 
@@ -1015,7 +1015,7 @@ int orc_node_search(uint32_t leaf, int rotation, const uint64_t *lo, const uint6
 
 /* Brute-force leaf search that stops hashing a trial at the first
  * collision; returns the seed found and the number of key hashes spent.
- * Used only to compare hash-evaluation counts (appendix figure on hash
+ * Used only to compare hash-evaluation counts (Appendix C figure on hash
  * function evaluations). */
 uint64_t orc_leaf_plain_early_exit(const uint64_t *lo, uint32_t m, uint64_t *evals) {
     uint64_t salt = orc_salt(0);

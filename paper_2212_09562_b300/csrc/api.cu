@@ -1,7 +1,7 @@
 // api.cu -- the C ABI of libmphf (declared in include/mphf.h).
 //
 // One build, all on the device (Section 2.2 of Bez et al. 2212.09562 in the
-// order of its parallel form, Section 4.3):
+// order of its parallel form, Section 5.3):
 //   fingerprint + histogram -> plan (nodes per bucket) -> prefix sums
 //   -> [host reads: node total, largest bucket, status]
 //   -> scatter by bucket -> persistent search kernel (splits, leaves)

@@ -1,6 +1,6 @@
 // build_kernels.cu -- device side of one or many RecSplit builds.
 //
-// Stages (Section 2.2 of Bez et al. 2212.09562, parallel form of Section 4.3):
+// Stages (Section 2.2 of Bez et al. 2212.09562, parallel form of Section 5.3):
 //   k_fp_hist   master hash of every key, bucket histogram
 //   k_plan      stored-node count per bucket (from the bucket size alone)
 //   k_scan_*    exclusive prefix sums (bucket offsets, node offsets, bits)
@@ -9,7 +9,7 @@
 //               searches of the inner nodes (all threads of the block try
 //               consecutive seeds), redistribution in shared memory, then
 //               leaf searches with one warp per leaf (plain or rotation
-//               fitting, Section 3)
+//               fitting, Section 4)
 //   k_gr_*      Golomb-Rice lengths and bit writes (fixed parts, then unary
 //               parts, in preorder per bucket)
 //   k_ef_*      Elias-Fano sequences and a rank directory for select
@@ -475,7 +475,7 @@ __device__ __forceinline__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, M
     }
 }
 
-// Leaf with rotation fitting (Section 3): lane = k, seed k*m; keys of A set
+// Leaf with rotation fitting (Section 4): lane = k, seed k*m; keys of A set
 // bits of a, keys of B bits of b; the smallest r with a | rot_m^r(b) full.
 // The lowest lane with a hit has the smallest k, hence the smallest k*m + r.
 template <class Mod>

@@ -6,7 +6,7 @@
 // part found by select in its unary region), hash to the child, add the
 // sizes of the children to its left and skip their subtrees (per-size
 // tables give their node counts and fixed bits).  At the leaf: the position
-// under the leaf's seed, plus the rotation r mod m for keys of B (Section 3).
+// under the leaf's seed, plus the rotation r mod m for keys of B (Section 4).
 #include <cuda_runtime.h>
 #include <stdint.h>
 

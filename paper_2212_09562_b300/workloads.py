@@ -3,7 +3,7 @@
 This module only draws random inputs: it holds none of the hashing or search
 arithmetic, so both the CUDA path and the CPU oracle can be fed from it.
 
-The paper builds on synthetic keys only (Section 5, experimental setup:
+The paper builds on synthetic keys only (Section 6, experimental setup:
 random 128-bit integers used directly, or random strings).  The workloads:
 
 * ``plain_l8``   n = 100,000 distinct uniform 64-bit keys, l = 8, b = 100, no rotation fitting

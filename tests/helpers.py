@@ -2,9 +2,9 @@
 
 The checker re-derives every node of a built function on tiny inputs and
 verifies, by brute force, that the stored value works and that every smaller
-value fails (the method stores the smallest working value; Section 4.1,
+value fails (the method stores the smallest working value; Section 5.1,
 "Bijections", on trying all rotations).  Rotation leaves are checked with the
-query-time rule of Section 3: keys of B move by +r mod m.
+query-time rule of Section 4: keys of B move by +r mod m.
 """
 from __future__ import annotations
 

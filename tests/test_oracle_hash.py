@@ -1,7 +1,7 @@
 """Oracle pins: hash function, fingerprint, bucket assignment.
 
 The paper asks only for a high-quality initial hash (Section 2.2, "Splitting
-Trees"; Section 5 uses random 128-bit master hash codes).  The hash chosen is
+Trees"; Section 6 uses random 128-bit master hash codes).  The hash chosen is
 the SplitMix64 output function, pinned against the generator's published
 outputs; the fingerprint is a Feistel network over it, pinned by inverting it.
 """

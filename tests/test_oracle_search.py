@@ -2,10 +2,10 @@
 
 * Brute force on tiny inputs: every stored value works and no smaller value
   does, for splits, plain leaves and rotation leaves (Section 2.2,
-  "Bijections"; Section 3; Section 4.1 on keeping the smallest stored number).
+  "Bijections"; Section 4; Section 5.1 on keeping the smallest stored number).
 * Statistics: mean trial counts match the closed forms (brute-force leaf
   l^l/l!, multinomial splits, rotation fitting by exact enumeration) and the
-  hash-evaluation ratio of the appendix figure on hash function evaluations.
+  hash-evaluation ratio of the Appendix C figure on hash function evaluations.
 * Error paths: duplicates, the search cap, bad parameters, oversized buckets.
 """
 import math
