@@ -138,6 +138,21 @@ int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out,
  * of range or already taken; 0 means a bijection.  Synchronises. */
 int mphf_verify(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad, void *stream);
 
+/* The same check without allocating: it uses a fixed scratch area that the
+ * library reserves in device memory (about 8.5 MB on every GPU where the
+ * library is loaded, held until the process exits).  For callers that cannot
+ * allocate device memory at this point: memory owned and budgeted by another
+ * allocator, latency-critical paths where allocation may stall the device,
+ * or code where allocation is not permitted.  The paper has no counterpart;
+ * this is a service of the library.
+ *   n <= MPHF_VERIFY_STATIC_MAX_KEYS, else MPHF_EINVAL (nothing is run).
+ *   Every call shares the scratch: calls whose work overlaps on the device
+ *   race and must be serialised.  The first call on a device looks up the
+ *   scratch address; make it before any stream capture.  Synchronises. */
+#define MPHF_VERIFY_STATIC_MAX_KEYS 1048576u
+int mphf_verify_static(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad,
+                       void *stream);
+
 int mphf_get_info(const mphf_t *h, mphf_info *info);
 
 /* Device arrays of a built function, owned by h:

@@ -28,6 +28,7 @@ EBUCKET = -7
 ENOTIMPL = -8
 ETIMEOUT = -9
 MAX_BUCKET = 4096
+VERIFY_STATIC_MAX_KEYS = 1 << 20
 DEFAULT_MAX_VALUE = (1 << 40) - 1
 
 _lock = threading.Lock()
@@ -83,6 +84,7 @@ SIGNATURES = {
     "mphf_build_host": (_I, [_P, _U64, _P, _P, _P]),
     "mphf_query": (_I, [_P, _P, _U64, _P, _P]),
     "mphf_verify": (_I, [_P, _P, _U64, _P, _P]),
+    "mphf_verify_static": (_I, [_P, _P, _U64, _P, _P]),
     "mphf_get_info": (_I, [_P, _P]),
     "mphf_get_values": (_I, [_P, _P, _P, _P, _P]),
     "mphf_get_bits": (_I, [_P, _P, _P, _P, _P]),
@@ -229,6 +231,16 @@ class MPHF:
         bad = ctypes.c_uint64()
         _check(lib().mphf_verify(self._h, keys.data_ptr() if n else None, n, ctypes.byref(bad),
                                  _stream(stream)), "mphf_verify")
+        return int(bad.value)
+
+    def verify_static(self, keys, stream=None) -> int:
+        """Like verify(), without allocating device memory: a fixed scratch area
+        reserved by the library serves every call (at most VERIFY_STATIC_MAX_KEYS
+        keys; calls must not overlap on the device)."""
+        n, _ = key_layout(keys)
+        bad = ctypes.c_uint64()
+        _check(lib().mphf_verify_static(self._h, keys.data_ptr() if n else None, n,
+                                        ctypes.byref(bad), _stream(stream)), "mphf_verify_static")
         return int(bad.value)
 
     # --- contents -----------------------------------------------------------
