@@ -25,10 +25,6 @@
 
 using namespace rs;
 
-#ifndef MPHF_LPT
-#define MPHF_LPT 1
-#endif
-
 namespace {
 
 struct DevTables {
@@ -109,10 +105,6 @@ int status_code(uint32_t st) {
     return MPHF_OK;
 }
 
-__global__ void k_items(WorkItem *items, uint32_t count, uint32_t inst) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-        items[i] = WorkItem{inst, i};
-}
 
 }  // namespace
 
@@ -172,183 +164,250 @@ int mphf_tau_table(uint32_t leaf_size, uint32_t rotation_fitting, uint32_t max_m
     return MPHF_OK;
 }
 
-int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, void *stream,
-                  mphf_t **out) {
-    if (!out || !p) return MPHF_EINVAL;
-    *out = nullptr;
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The build engine: any number of independent builds ("jobs") go through the
+// same phases on one stream, with one host read between phases for all of
+// them and ONE persistent search launch over the buckets of every job
+// (largest buckets first across jobs, mixed leaf sizes in the same launch).
+namespace {
+
+struct Job {
+    const void *d_keys = nullptr;
+    uint64_t n = 0;
+    mphf_build_params p{};
+    mphf_t *h = nullptr;
+    int rc = MPHF_OK;
+    uint64_t nb = 0, maxv = 0;
+    uint64_t *lo_s = nullptr, *counters = nullptr;
+    uint8_t *bb_s = nullptr;
+    uint32_t *cursor = nullptr, *small = nullptr;  // small: status, max bucket, spare
+    uint16_t *node_m = nullptr;
+    uint64_t n_nodes = 0;
+};
+
+int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
+    if (!p) return MPHF_EINVAL;
     if (p->leaf_size < 2 || p->leaf_size > MPHF_MAX_LEAF || p->bucket_size < 1 ||
         p->bucket_size > MPHF_MAX_BUCKET_SIZE || (p->key_bytes != 8 && p->key_bytes != 16) ||
         n >= (1ull << 32) || (n > 0 && !d_keys) || ((uintptr_t)d_keys & 7))
         return MPHF_EINVAL;
-    if (p->threads_per_block && (p->threads_per_block % 32 || p->threads_per_block > 512 ||
-                                 p->threads_per_block < 64))
+    if (p->threads_per_block &&
+        (p->threads_per_block % 32 || p->threads_per_block > 512 || p->threads_per_block < 64))
         return MPHF_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
-    mphf_t *h = new (std::nothrow) mphf;
-    if (!h) return MPHF_ENOMEM;
-    cudaGetDevice(&h->device);
-    if (p->allocator) {
-        h->alloc = *p->allocator;
-        h->has_alloc = true;
-    }
-    Mem mem{h->has_alloc ? &h->alloc : nullptr, st};
-    const uint32_t leaf = p->leaf_size, rot = p->rotation_fitting ? 1 : 0;
-    const uint64_t nb = (n + p->bucket_size - 1) / p->bucket_size;
-    const uint64_t maxv = p->max_value ? p->max_value : MPHF_DEFAULT_MAX_VALUE;
-    h->info.n = n;
-    h->info.nb = nb;
-    h->info.leaf_size = leaf;
-    h->info.bucket_size = p->bucket_size;
-    h->info.key_bytes = p->key_bytes;
-    h->info.rotation_fitting = rot;
-    int rc = device_tables(h->device, leaf, rot, &h->tabs);
-    if (rc) {
-        release(h);
-        return rc;
-    }
+    return MPHF_OK;
+}
 
-    // temporaries
-    uint64_t *node_cnt = nullptr, *scan_tmp = nullptr, *lo_s = nullptr, *counters = nullptr;
-    uint8_t *bb_s = nullptr;
-    uint32_t *cursor = nullptr, *small = nullptr;
-    uint16_t *node_m = nullptr;
+void free_job_scratch(Job &j, Mem &mem) {
+    mem.put(j.lo_s);
+    mem.put(j.bb_s);
+    mem.put(j.cursor);
+    mem.put(j.small);
+    mem.put(j.node_m);
+    mem.put(j.counters);
+    j.lo_s = j.counters = nullptr;
+    j.bb_s = nullptr;
+    j.cursor = j.small = nullptr;
+    j.node_m = nullptr;
+}
+
+void fail_job(Job &j, int rc, Mem &mem) {
+    if (j.rc == MPHF_OK) j.rc = rc;
+    free_job_scratch(j, mem);
+    if (j.h) {
+        release(j.h);
+        j.h = nullptr;
+    }
+}
+
+// Runs every job; afterwards each job has rc set and, if rc is OK, h built.
+// Returns a code for failures that affect all jobs (CUDA errors), else OK.
+int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shared_alloc,
+             uint32_t threads, uint32_t blocks_per_sm) {
+    Mem mem{shared_alloc, st};
+    int grc = MPHF_OK;
+    const size_t J = jobs.size();
+    uint64_t *host = nullptr, *scan_tmp = nullptr, *size_hist = nullptr;
+    uint32_t *size_cursor = nullptr, *head = nullptr;
     InstDesc *d_inst = nullptr;
     WorkItem *items = nullptr;
-    uint64_t *host_small = nullptr;
-    uint64_t *size_hist = nullptr;
-    uint32_t *size_cursor = nullptr;
+    std::vector<InstDesc> hinst;
+    std::vector<uint32_t> inst_job;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint64_t max_nb = 0, total_items = 0, total_slots = 0;
+    uint32_t max_m = 0;
+    float ms[4] = {0, 0, 0, 0};
+#define CU(x)                    \
+    do {                         \
+        if ((x) != cudaSuccess) { \
+            cudaGetLastError();  \
+            grc = MPHF_ECUDA;    \
+            goto done;           \
+        }                        \
+    } while (0)
     for (auto &e : ev) cudaEventCreate(&e);
     cudaEventRecord(ev[0], st);
+    for (auto &j : jobs) max_nb = j.nb > max_nb ? j.nb : max_nb;
+    CU(cudaMallocHost(&host, 8 * 4 * (J ? J : 1)));
+    scan_tmp = (uint64_t *)mem.get((scan_tmp_words((max_nb + 2 > 4098 ? max_nb + 2 : 4098)) + 64) * 8);
+    size_hist = (uint64_t *)mem.get(4098 * 8);
+    size_cursor = (uint32_t *)mem.get(4097 * 4);
+    head = (uint32_t *)mem.get(64);
+    if (!scan_tmp || !size_hist || !size_cursor || !head) {
+        grc = MPHF_ENOMEM;
+        goto done;
+    }
+    CU(cudaMemsetAsync(size_hist, 0, 4098 * 8, st));
+    CU(cudaMemsetAsync(size_cursor, 0, 4097 * 4, st));
+    CU(cudaMemsetAsync(head, 0, 64, st));
 
-    const uint64_t scan_words = scan_tmp_words(nb + 2 > 4096 ? nb + 2 : 4096) + 64;
-#define CK(x)                   \
-    do {                        \
-        if (!(x)) {             \
-            rc = MPHF_ENOMEM;   \
-            goto done;          \
-        }                       \
-    } while (0)
-#define CU(x)                                   \
-    do {                                        \
-        if ((x) != cudaSuccess) {               \
-            cudaGetLastError();                 \
-            rc = MPHF_ECUDA;                    \
-            goto done;                          \
-        }                                       \
-    } while (0)
-    {
-        CK(h->cum_keys = (uint64_t *)mem.get((nb + 1) * 8));
-        CK(h->node_off = (uint64_t *)mem.get((nb + 1) * 8));
-        CK(h->bit_pos = (uint64_t *)mem.get((nb + 1) * 8));
-        CK(node_cnt = h->node_off);
-        CK(scan_tmp = (uint64_t *)mem.get(scan_words * 8));
-        CK(cursor = (uint32_t *)mem.get((nb + 1) * 4));
-        CK(small = (uint32_t *)mem.get(64));
-        CK(lo_s = (uint64_t *)mem.get(n * 8));
-        CK(bb_s = (uint8_t *)mem.get(n));
-        CK(counters = (uint64_t *)mem.get(8 * 8));
-        CK(size_hist = (uint64_t *)mem.get(4098 * 8));
-        CK(size_cursor = (uint32_t *)mem.get(4097 * 4));
-        CU(cudaMemsetAsync(size_hist, 0, 4098 * 8, st));
-        CU(cudaMemsetAsync(size_cursor, 0, 4097 * 4, st));
-        CU(cudaMallocHost(&host_small, 64));
+    // phase 1: fingerprints, bucket sizes, plan, offsets (per job, no host reads)
+    for (auto &j : jobs) {
+        if (j.rc) continue;
+        mphf_t *h = j.h;
+        Mem jm{h->has_alloc ? &h->alloc : nullptr, st};
+        const uint64_t nb = j.nb;
+        h->cum_keys = (uint64_t *)jm.get((nb + 1) * 8);
+        h->node_off = (uint64_t *)jm.get((nb + 1) * 8);
+        h->bit_pos = (uint64_t *)jm.get((nb + 1) * 8);
+        j.cursor = (uint32_t *)mem.get((nb + 1) * 4);
+        j.small = (uint32_t *)mem.get(64);
+        j.lo_s = (uint64_t *)mem.get(j.n * 8);
+        j.bb_s = (uint8_t *)mem.get(j.n);
+        j.counters = (uint64_t *)mem.get(64);
+        if (!h->cum_keys || !h->node_off || !h->bit_pos || !j.cursor || !j.small || !j.lo_s ||
+            !j.bb_s || !j.counters) {
+            fail_job(j, MPHF_ENOMEM, mem);
+            continue;
+        }
         CU(cudaMemsetAsync(h->cum_keys, 0, (nb + 1) * 8, st));
         CU(cudaMemsetAsync(h->node_off, 0, (nb + 1) * 8, st));
-        CU(cudaMemsetAsync(cursor, 0, (nb + 1) * 4, st));
-        CU(cudaMemsetAsync(small, 0, 64, st));
-        CU(cudaMemsetAsync(counters, 0, 64, st));
-
-        // fingerprints, bucket sizes, plan, offsets
-        launch_fp_hist(d_keys, n, p->key_bytes, nb, h->cum_keys, st);
-        launch_plan(h->cum_keys, nb, h->tabs.nodes, node_cnt, small, small + 1, size_hist, st);
+        CU(cudaMemsetAsync(j.cursor, 0, (nb + 1) * 4, st));
+        CU(cudaMemsetAsync(j.small, 0, 64, st));
+        CU(cudaMemsetAsync(j.counters, 0, 64, st));
+        launch_fp_hist(j.d_keys, j.n, j.p.key_bytes, nb, h->cum_keys, st);
+        launch_plan(h->cum_keys, nb, h->tabs.nodes, h->node_off, j.small, j.small + 1, size_hist, st);
         launch_exclusive_scan(h->cum_keys, nb + 1, scan_tmp, st);
-        launch_exclusive_scan(node_cnt, nb + 1, scan_tmp, st);
-        launch_exclusive_scan(size_hist, 4098, scan_tmp, st);
+        launch_exclusive_scan(h->node_off, nb + 1, scan_tmp, st);
         CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(host_small, node_cnt + nb, 8, cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(host_small + 1, small, 8, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        cudaEventRecord(ev[1], st);
-        const uint64_t n_nodes = host_small[0];
-        const uint32_t status0 = (uint32_t)host_small[1], max_m = (uint32_t)(host_small[1] >> 32);
-        h->info.n_nodes = n_nodes;
-        h->info.max_bucket = max_m;
-        if (status0) {
-            rc = status_code(status0);
+    }
+    for (size_t i = 0; i < J; i++) {
+        Job &j = jobs[i];
+        if (j.rc) continue;
+        total_slots += j.nb;  // every bucket of these jobs is counted in size_hist
+        CU(cudaMemcpyAsync(host + 4 * i, j.h->node_off + j.nb, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(host + 4 * i + 1, j.small, 8, cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+    cudaEventRecord(ev[1], st);
+
+    // phase 2: group keys by bucket; one persistent search over every job's buckets
+    launch_exclusive_scan(size_hist, 4098, scan_tmp, st);
+    for (size_t i = 0; i < J; i++) {
+        Job &j = jobs[i];
+        if (j.rc) continue;
+        mphf_t *h = j.h;
+        j.n_nodes = host[4 * i];
+        const uint32_t status = (uint32_t)host[4 * i + 1];
+        const uint32_t mm = (uint32_t)(host[4 * i + 1] >> 32);
+        h->info.n_nodes = j.n_nodes;
+        h->info.max_bucket = mm;
+        if (status) {
+            fail_job(j, status_code(status), mem);
+            continue;
+        }
+        Mem jm{h->has_alloc ? &h->alloc : nullptr, st};
+        h->values = (uint64_t *)jm.get(j.n_nodes * 8);
+        j.node_m = (uint16_t *)mem.get(j.n_nodes * 2);
+        if (!h->values || !j.node_m) {
+            fail_job(j, MPHF_ENOMEM, mem);
+            continue;
+        }
+        launch_scatter(j.d_keys, j.n, j.p.key_bytes, j.nb, h->cum_keys, j.cursor, j.lo_s, j.bb_s, st);
+        InstDesc d;
+        memset(&d, 0, sizeof(d));
+        d.lo = j.lo_s;
+        d.bb = j.bb_s;
+        d.bucket_off = h->cum_keys;
+        d.node_off = h->node_off;
+        d.nodes_tab = h->tabs.nodes;
+        d.values = h->values;
+        d.node_m = j.node_m;
+        d.status = j.small;
+        d.max_value = j.maxv;
+        d.leaf = j.p.leaf_size;
+        d.rotation = j.p.rotation_fitting ? 1 : 0;
+        d.nb = (uint32_t)j.nb;
+        d.k30 = 1u << 2;
+        d.k27 = 1u << 5;
+        d.k31 = 1u << 1;
+        Shape shp = make_shape(j.p.leaf_size);
+        d.red[0] = (uint32_t)((1ull << 32) % j.p.leaf_size);
+        d.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
+        d.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
+        inst_job.push_back((uint32_t)i);
+        hinst.push_back(d);
+        total_items += j.nb;
+        max_m = mm > max_m ? mm : max_m;
+    }
+    if (total_slots > 0xFFFFFFFFull) {
+        grc = MPHF_EINVAL;
+        goto done;
+    }
+    if (total_items > 0) {
+        // slots of jobs that failed their plan stay empty (all-ones: skipped)
+        d_inst = (InstDesc *)mem.get(hinst.size() * sizeof(InstDesc));
+        items = (WorkItem *)mem.get(total_slots * sizeof(WorkItem));
+        if (!d_inst || !items) {
+            grc = MPHF_ENOMEM;
             goto done;
         }
-
-        // group keys by bucket, search every bucket
-        CK(h->values = (uint64_t *)mem.get(n_nodes * 8));
-        CK(node_m = (uint16_t *)mem.get(n_nodes * 2));
-        launch_scatter(d_keys, n, p->key_bytes, nb, h->cum_keys, cursor, lo_s, bb_s, st);
-        if (nb > 0) {
-            CK(items = (WorkItem *)mem.get(nb * sizeof(WorkItem)));
-            CK(d_inst = (InstDesc *)mem.get(sizeof(InstDesc)));
-            InstDesc hd;
-            hd.lo = lo_s;
-            hd.bb = bb_s;
-            hd.bucket_off = h->cum_keys;
-            hd.node_off = h->node_off;
-            hd.nodes_tab = h->tabs.nodes;
-            hd.values = h->values;
-            hd.node_m = node_m;
-            hd.status = small;
-            hd.max_value = maxv;
-            hd.leaf = leaf;
-            hd.rotation = rot;
-            hd.nb = (uint32_t)nb;
-            hd.k30 = 1u << 2;
-            hd.k27 = 1u << 5;
-            hd.k31 = 1u << 1;
-            {
-                Shape shp = make_shape(leaf);
-                hd.red[0] = (uint32_t)((1ull << 32) % leaf);
-                hd.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
-                hd.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
-            }
-            CU(cudaMemcpyAsync(d_inst, &hd, sizeof(hd), cudaMemcpyHostToDevice, st));
-#if MPHF_LPT
-            launch_items_by_size(h->cum_keys, nb, size_hist, size_cursor, items, 0, st);
-#else
-            k_items<<<(uint32_t)((nb + 255) / 256 < 4096 ? (nb + 255) / 256 : 4096), 256, 0, st>>>(
-                items, (uint32_t)nb, 0);
-            note_launches(1);
-#endif
-            SearchLaunch L = plan_search_launch(max_m, (uint32_t)nb, p->threads_per_block,
-                                                p->blocks_per_sm);
-            cudaEventRecord(ev[2], st);
-            launch_search(d_inst, items, (uint32_t)nb, small + 2, L, st);
-            CU(cudaGetLastError());
-        } else {
-            cudaEventRecord(ev[2], st);
+        CU(cudaMemsetAsync(items, 0xFF, total_slots * sizeof(WorkItem), st));
+        CU(cudaMemcpyAsync(d_inst, hinst.data(), hinst.size() * sizeof(InstDesc),
+                           cudaMemcpyHostToDevice, st));
+        for (size_t k = 0; k < inst_job.size(); k++) {
+            Job &j = jobs[inst_job[k]];
+            launch_items_by_size(j.h->cum_keys, j.nb, size_hist, size_cursor, items, (uint32_t)k, st);
         }
-        cudaEventRecord(ev[3], st);
-
-        // Golomb-Rice lengths and offsets
-        CU(cudaMemsetAsync(h->bit_pos, 0, (nb + 1) * 8, st));
-        launch_gr_lengths(h->values, node_m, h->node_off, nb, h->tabs.tau, h->bit_pos, st);
-        launch_exclusive_scan(h->bit_pos, nb + 1, scan_tmp, st);
+        SearchLaunch L = plan_search_launch(max_m, (uint32_t)total_slots, threads, blocks_per_sm);
+        cudaEventRecord(ev[2], st);
+        launch_search(d_inst, items, (uint32_t)total_slots, head, L, st);
         CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(host_small, h->bit_pos + nb, 8, cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(host_small + 1, small, 8, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        const uint64_t gr_bits = host_small[0];
-        const uint32_t status1 = (uint32_t)host_small[1];
-        if (status1) {
-            rc = status_code(status1);
-            goto done;
+    } else {
+        cudaEventRecord(ev[2], st);
+    }
+    cudaEventRecord(ev[3], st);
+
+    // phase 3: Golomb-Rice lengths and offsets
+    for (size_t i = 0; i < J; i++) {
+        Job &j = jobs[i];
+        if (j.rc) continue;
+        mphf_t *h = j.h;
+        CU(cudaMemsetAsync(h->bit_pos, 0, (j.nb + 1) * 8, st));
+        launch_gr_lengths(h->values, j.node_m, h->node_off, j.nb, h->tabs.tau, h->bit_pos, st);
+        launch_exclusive_scan(h->bit_pos, j.nb + 1, scan_tmp, st);
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(host + 4 * i, h->bit_pos + j.nb, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(host + 4 * i + 1, j.small, 8, cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+
+    // phase 4: Golomb-Rice bits, Elias-Fano, rank directories, statistics
+    for (size_t i = 0; i < J; i++) {
+        Job &j = jobs[i];
+        if (j.rc) continue;
+        mphf_t *h = j.h;
+        const uint32_t status = (uint32_t)host[4 * i + 1];
+        if (status) {
+            fail_job(j, status_code(status), mem);
+            continue;
         }
+        const uint64_t gr_bits = host[4 * i];
+        Mem jm{h->has_alloc ? &h->alloc : nullptr, st};
         h->info.gr_bits = gr_bits;
         h->info.gr_words = (gr_bits + 63) / 64;
-        CK(h->gr = (uint64_t *)mem.get(h->info.gr_words * 8 + 8));
-        CU(cudaMemsetAsync(h->gr, 0, h->info.gr_words * 8 + 8, st));
-        launch_gr_write(h->values, node_m, h->node_off, h->bit_pos, nb, h->tabs.tau,
-                        h->tabs.fixed, h->cum_keys, h->gr, st);
-
-        // Elias-Fano over bucket prefix sums and bucket bit positions
-        EfDims e0 = ef_dims(nb + 1, n), e1 = ef_dims(nb + 1, gr_bits);
+        EfDims e0 = ef_dims(j.nb + 1, j.n), e1 = ef_dims(j.nb + 1, gr_bits);
         h->info.ef_low_bits[0] = e0.L;
         h->info.ef_low_bits[1] = e1.L;
         h->info.ef_seq_words[0] = e0.low_words;
@@ -356,60 +415,122 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, vo
         h->info.ef_seq_words[2] = e1.low_words;
         h->info.ef_seq_words[3] = e1.high_words;
         h->info.ef_words = e0.low_words + e0.high_words + e1.low_words + e1.high_words;
-        CK(h->ef = (uint64_t *)mem.get(h->info.ef_words * 8 + 8));
-        CU(cudaMemsetAsync(h->ef, 0, h->info.ef_words * 8 + 8, st));
-        uint64_t *lo0 = h->ef, *hi0 = lo0 + e0.low_words, *lo1 = hi0 + e0.high_words,
-                 *hi1 = lo1 + e1.low_words;
-        launch_ef_write(h->cum_keys, nb + 1, e0.L, lo0, hi0, st);
-        launch_ef_write(h->bit_pos, nb + 1, e1.L, lo1, hi1, st);
         h->ef_dir_len[0] = e0.high_words + 1;
         h->ef_dir_len[1] = e1.high_words + 1;
-        CK(h->ef_dir = (uint64_t *)mem.get((h->ef_dir_len[0] + h->ef_dir_len[1]) * 8));
+        h->gr = (uint64_t *)jm.get(h->info.gr_words * 8 + 8);
+        h->ef = (uint64_t *)jm.get(h->info.ef_words * 8 + 8);
+        h->ef_dir = (uint64_t *)jm.get((h->ef_dir_len[0] + h->ef_dir_len[1]) * 8);
+        if (!h->gr || !h->ef || !h->ef_dir) {
+            fail_job(j, MPHF_ENOMEM, mem);
+            continue;
+        }
+        CU(cudaMemsetAsync(h->gr, 0, h->info.gr_words * 8 + 8, st));
+        CU(cudaMemsetAsync(h->ef, 0, h->info.ef_words * 8 + 8, st));
+        launch_gr_write(h->values, j.node_m, h->node_off, h->bit_pos, j.nb, h->tabs.tau,
+                        h->tabs.fixed, h->cum_keys, h->gr, st);
+        uint64_t *lo0 = h->ef, *hi0 = lo0 + e0.low_words, *lo1 = hi0 + e0.high_words,
+                 *hi1 = lo1 + e1.low_words;
+        launch_ef_write(h->cum_keys, j.nb + 1, e0.L, lo0, hi0, st);
+        launch_ef_write(h->bit_pos, j.nb + 1, e1.L, lo1, hi1, st);
         launch_rank_dir(hi0, e0.high_words, h->ef_dir, scan_tmp, st);
         launch_rank_dir(hi1, e1.high_words, h->ef_dir + h->ef_dir_len[0], scan_tmp, st);
-        launch_stats(h->values, node_m, n_nodes, leaf, rot, counters, st);
+        launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.rotation_fitting ? 1 : 0,
+                     j.counters, st);
         CU(cudaGetLastError());
-        cudaEventRecord(ev[4], st);
-        uint64_t hc[8];
-        CU(cudaMemcpyAsync(host_small, counters, 64, cudaMemcpyDeviceToHost, st));
+    }
+    cudaEventRecord(ev[4], st);
+    {
+        std::vector<uint64_t> hc(8 * (J ? J : 1));
+        for (size_t i = 0; i < J; i++)
+            if (!jobs[i].rc) CU(cudaMemcpyAsync(&hc[8 * i], jobs[i].counters, 64, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        memcpy(hc, host_small, 64);
-        for (int k = 0; k < 4; k++) {
-            h->stats.trials[k] = hc[k];
-            h->stats.evals[k] = hc[4 + k];
+        cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+        cudaEventElapsedTime(&ms[1], ev[2], ev[3]);
+        cudaEventElapsedTime(&ms[2], ev[3], ev[4]);
+        cudaEventElapsedTime(&ms[3], ev[0], ev[4]);
+        for (size_t i = 0; i < J; i++) {
+            Job &j = jobs[i];
+            if (j.rc) continue;
+            for (int k = 0; k < 4; k++) {
+                j.h->stats.trials[k] = hc[8 * i + k];
+                j.h->stats.evals[k] = hc[8 * i + 4 + k];
+            }
+            j.h->stats.ms_plan = ms[0];
+            j.h->stats.ms_search = ms[1];
+            j.h->stats.ms_pack = ms[2];
+            j.h->stats.ms_total = ms[3];
         }
-        cudaEventElapsedTime(&h->stats.ms_plan, ev[0], ev[1]);
-        cudaEventElapsedTime(&h->stats.ms_search, ev[2], ev[3]);
-        cudaEventElapsedTime(&h->stats.ms_pack, ev[3], ev[4]);
-        cudaEventElapsedTime(&h->stats.ms_total, ev[0], ev[4]);
-        rc = MPHF_OK;
     }
 done:
-#undef CK
 #undef CU
+    cudaStreamSynchronize(st);
+    for (auto &j : jobs) {
+        free_job_scratch(j, mem);
+        if (grc != MPHF_OK && j.rc == MPHF_OK) fail_job(j, grc, mem);
+    }
     mem.put(scan_tmp);
-    mem.put(cursor);
-    mem.put(small);
-    mem.put(lo_s);
-    mem.put(bb_s);
-    mem.put(counters);
-    mem.put(node_m);
-    mem.put(items);
-    mem.put(d_inst);
     mem.put(size_hist);
     mem.put(size_cursor);
-    if (host_small) {
-        cudaStreamSynchronize(st);
-        cudaFreeHost(host_small);
-    }
+    mem.put(head);
+    mem.put(d_inst);
+    mem.put(items);
+    cudaStreamSynchronize(st);
+    if (host) cudaFreeHost(host);
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
-    if (rc != MPHF_OK) {
-        cudaStreamSynchronize(st);
-        release(h);
-        return rc;
+    return grc;
+}
+
+// Creates the handle of a job (parameters checked, tables ready).
+void start_job(Job &j, const void *d_keys, uint64_t n, const mphf_build_params &p) {
+    j.d_keys = d_keys;
+    j.n = n;
+    j.p = p;
+    j.rc = check_params(d_keys, n, &p);
+    if (j.rc) return;
+    mphf_t *h = new (std::nothrow) mphf;
+    if (!h) {
+        j.rc = MPHF_ENOMEM;
+        return;
     }
-    *out = h;
+    cudaGetDevice(&h->device);
+    if (p.allocator) {
+        h->alloc = *p.allocator;
+        h->has_alloc = true;
+    }
+    j.h = h;
+    j.nb = (n + p.bucket_size - 1) / p.bucket_size;
+    j.maxv = p.max_value ? p.max_value : MPHF_DEFAULT_MAX_VALUE;
+    h->info.n = n;
+    h->info.nb = j.nb;
+    h->info.leaf_size = p.leaf_size;
+    h->info.bucket_size = p.bucket_size;
+    h->info.key_bytes = p.key_bytes;
+    h->info.rotation_fitting = p.rotation_fitting ? 1 : 0;
+    int rc = device_tables(h->device, p.leaf_size, h->info.rotation_fitting, &h->tabs);
+    if (rc) {
+        release(h);
+        j.h = nullptr;
+        j.rc = rc;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *p, void *stream,
+                  mphf_t **out) {
+    if (!out || !p) return MPHF_EINVAL;
+    *out = nullptr;
+    std::vector<Job> jobs(1);
+    start_job(jobs[0], d_keys, n, *p);
+    if (jobs[0].rc) return jobs[0].rc;
+    int grc = run_jobs(jobs, (cudaStream_t)stream, p->allocator, p->threads_per_block,
+                       p->blocks_per_sm);
+    if (grc) return grc;
+    if (jobs[0].rc) return jobs[0].rc;
+    *out = jobs[0].h;
     return MPHF_OK;
 }
 
@@ -580,8 +701,8 @@ uint64_t mphf_kernel_launches(void) { return launches_total(); }
 
 int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream, mphf_t **outs,
                      int *statuses) {
-    if ((count && (!descs || !outs)) ) return MPHF_EINVAL;
-    int first = MPHF_OK;
+    if (count && (!descs || !outs)) return MPHF_EINVAL;
+    std::vector<Job> jobs(count);
     for (uint32_t i = 0; i < count; i++) {
         mphf_build_params p;
         mphf_default_params(&p);
@@ -590,8 +711,15 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
         p.key_bytes = descs[i].key_bytes;
         p.rotation_fitting = descs[i].rotation_fitting;
         p.max_value = descs[i].max_value ? descs[i].max_value : MPHF_DEFAULT_MAX_VALUE;
-        int rc = mphf_build_ex(descs[i].d_keys, descs[i].n, &p, stream, &outs[i]);
+        outs[i] = nullptr;
+        start_job(jobs[i], descs[i].d_keys, descs[i].n, p);
+    }
+    int grc = run_jobs(jobs, (cudaStream_t)stream, nullptr, 0, 0);
+    int first = grc;
+    for (uint32_t i = 0; i < count; i++) {
+        int rc = jobs[i].rc ? jobs[i].rc : grc;
         if (statuses) statuses[i] = rc;
+        if (rc == MPHF_OK) outs[i] = jobs[i].h;
         if (rc && first == MPHF_OK) first = rc;
     }
     return first;

@@ -770,6 +770,7 @@ __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, const Wor
         __syncthreads();
         if (it >= nitems) break;
         const WorkItem w = items[it];
+        if (w.inst == 0xFFFFFFFFu) continue;  // empty slot (its build failed its plan)
         const InstDesc d = insts[w.inst];
         switch (d.leaf) {
             case 8: process_bucket<8>(d, w.bucket, A, S); break;

@@ -26,7 +26,7 @@ struct InstDesc {
     uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
 };
 
-// One unit of work: a bucket of an instance.
+// One unit of work: a bucket of an instance (inst = all ones: an empty slot).
 struct WorkItem {
     uint32_t inst, bucket;
 };
