@@ -208,6 +208,45 @@ typedef struct {
 int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream, mphf_t **outs,
                      int *statuses);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a build server with continuous batching.  Requests are queued;
+ * executor threads (one CUDA stream each) take every pending request that
+ * fits into free device memory and build them together as one batch (one
+ * persistent search over all their buckets).  A batch is admitted while
+ * another is still on the device, so their work overlaps.  Results are
+ * identical to building each request alone.  No device-side waiting is
+ * involved; every host wait is bounded by the caller's timeout. */
+typedef struct mphf_server mphf_server_t;
+
+typedef struct {
+    uint32_t executors;          /* batches on the device at once (default 2)          */
+    uint32_t max_batch;          /* requests per batch (default 64)                    */
+    uint64_t hbm_reserve_bytes;  /* device memory kept free (default 1 GiB)            */
+} mphf_server_cfg;
+
+/* Submit/admit/finish times of a request, seconds since the server started. */
+typedef struct {
+    double submitted, admitted, finished;
+} mphf_request_times;
+
+/* cfg NULL = defaults.  The server uses the current device. */
+int mphf_server_create(const mphf_server_cfg *cfg, mphf_server_t **out);
+
+/* Queues a build.  The keys (device memory) must stay valid until the
+ * request is finished.  *ticket identifies it for mphf_server_poll. */
+int mphf_server_submit(mphf_server_t *s, const mphf_build_desc *desc, uint64_t *ticket);
+
+/* Waits up to timeout_ms for the request (0 = do not wait).  Returns
+ * MPHF_ETIMEOUT if it is not finished yet, else MPHF_OK with *status the
+ * build's code and, on success, *out the built function (owned by the caller
+ * from now on).  A finished ticket can be polled once. */
+int mphf_server_poll(mphf_server_t *s, uint64_t ticket, uint32_t timeout_ms, mphf_t **out,
+                     int *status, mphf_request_times *times);
+
+/* Finishes every queued request, then stops the executors.  Functions built
+ * but never polled are freed. */
+int mphf_server_destroy(mphf_server_t *s);
+
 #ifdef __cplusplus
 }
 #endif

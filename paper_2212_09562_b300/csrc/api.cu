@@ -13,9 +13,14 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -723,6 +728,206 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
         if (rc && first == MPHF_OK) first = rc;
     }
     return first;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Build server with continuous batching.
+namespace {
+
+struct ServerRequest {
+    uint64_t ticket = 0;
+    mphf_build_desc desc{};
+    mphf_request_times t{};
+    int status = MPHF_OK;
+    mphf_t *out = nullptr;
+    bool done = false;
+};
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Device memory a build needs besides its keys: grouped lo words and bits,
+// node values and sizes, offsets, packed output (about 11 bytes per key).
+uint64_t build_bytes(const mphf_build_desc &d) {
+    uint64_t nb = d.bucket_size ? (d.n + d.bucket_size - 1) / d.bucket_size : 0;
+    return 16 * d.n + 48 * nb + (1u << 20);
+}
+
+}  // namespace
+
+struct mphf_server {
+    int device = 0;
+    mphf_server_cfg cfg{};
+    std::chrono::steady_clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerRequest *> pending;
+    std::unordered_map<uint64_t, ServerRequest *> requests;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    uint64_t next_ticket = 1, reserved = 0;
+    uint32_t inflight = 0;
+    bool stop = false;
+};
+
+static void server_worker(mphf_server_t *S, int w) {
+    cudaSetDevice(S->device);
+    cudaStream_t st = S->streams[w];
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(50),
+                            [&] { return S->stop || !S->pending.empty(); });
+        if (S->pending.empty()) {
+            if (S->stop) break;
+            continue;
+        }
+        // admission: pending requests in arrival order while device memory allows
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = 0;
+        }
+        int64_t budget = (int64_t)free_b - (int64_t)S->cfg.hbm_reserve_bytes - (int64_t)S->reserved;
+        std::vector<ServerRequest *> batch;
+        uint64_t need = 0;
+        while (!S->pending.empty() && batch.size() < S->cfg.max_batch) {
+            uint64_t b = build_bytes(S->pending.front()->desc);
+            bool fits = (int64_t)(need + b) <= budget;
+            // a request that never fits still runs when nothing else is on the device
+            if (!fits && !(batch.empty() && S->inflight == 0)) break;
+            batch.push_back(S->pending.front());
+            S->pending.pop_front();
+            need += b;
+        }
+        if (batch.empty()) {  // wait for memory to come back
+            S->cv_done.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        S->reserved += need;
+        S->inflight++;
+        const double t_admit = seconds_since(S->t0);
+        for (auto *r : batch) r->t.admitted = t_admit;
+        lk.unlock();
+
+        std::vector<Job> jobs(batch.size());
+        for (size_t i = 0; i < batch.size(); i++) {
+            const mphf_build_desc &d = batch[i]->desc;
+            mphf_build_params p;
+            mphf_default_params(&p);
+            p.leaf_size = d.leaf_size;
+            p.bucket_size = d.bucket_size;
+            p.key_bytes = d.key_bytes;
+            p.rotation_fitting = d.rotation_fitting;
+            p.max_value = d.max_value ? d.max_value : MPHF_DEFAULT_MAX_VALUE;
+            start_job(jobs[i], d.d_keys, d.n, p);
+        }
+        int grc = run_jobs(jobs, st, nullptr, 0, 0);
+
+        lk.lock();
+        const double t_done = seconds_since(S->t0);
+        for (size_t i = 0; i < batch.size(); i++) {
+            ServerRequest *r = batch[i];
+            r->status = jobs[i].rc ? jobs[i].rc : grc;
+            r->out = r->status == MPHF_OK ? jobs[i].h : nullptr;
+            r->t.finished = t_done;
+            r->done = true;
+        }
+        S->reserved -= need;
+        S->inflight--;
+        S->cv_done.notify_all();
+    }
+}
+
+extern "C" {
+
+int mphf_server_create(const mphf_server_cfg *cfg, mphf_server_t **out) {
+    if (!out) return MPHF_EINVAL;
+    *out = nullptr;
+    mphf_server_t *S = new (std::nothrow) mphf_server;
+    if (!S) return MPHF_ENOMEM;
+    S->cfg.executors = cfg && cfg->executors ? cfg->executors : 2;
+    S->cfg.max_batch = cfg && cfg->max_batch ? cfg->max_batch : 64;
+    S->cfg.hbm_reserve_bytes = cfg && cfg->hbm_reserve_bytes ? cfg->hbm_reserve_bytes : (1ull << 30);
+    if (S->cfg.executors > 16) {
+        delete S;
+        return MPHF_EINVAL;
+    }
+    S->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return MPHF_ECUDA;
+    }
+    for (uint32_t w = 0; w < S->cfg.executors; w++) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto x : S->streams) cudaStreamDestroy(x);
+            delete S;
+            return MPHF_ECUDA;
+        }
+        S->streams.push_back(st);
+    }
+    for (uint32_t w = 0; w < S->cfg.executors; w++) S->workers.emplace_back(server_worker, S, (int)w);
+    *out = S;
+    return MPHF_OK;
+}
+
+int mphf_server_submit(mphf_server_t *S, const mphf_build_desc *desc, uint64_t *ticket) {
+    if (!S || !desc || !ticket) return MPHF_EINVAL;
+    ServerRequest *r = new (std::nothrow) ServerRequest;
+    if (!r) return MPHF_ENOMEM;
+    r->desc = *desc;
+    std::lock_guard<std::mutex> g(S->mu);
+    if (S->stop) {
+        delete r;
+        return MPHF_EBUSY;
+    }
+    r->ticket = S->next_ticket++;
+    r->t.submitted = seconds_since(S->t0);
+    S->requests[r->ticket] = r;
+    S->pending.push_back(r);
+    *ticket = r->ticket;
+    S->cv_work.notify_one();
+    return MPHF_OK;
+}
+
+int mphf_server_poll(mphf_server_t *S, uint64_t ticket, uint32_t timeout_ms, mphf_t **out,
+                     int *status, mphf_request_times *times) {
+    if (!S || !out || !status) return MPHF_EINVAL;
+    *out = nullptr;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->requests.find(ticket);
+    if (it == S->requests.end()) return MPHF_EINVAL;
+    ServerRequest *r = it->second;
+    if (!r->done)
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; });
+    if (!r->done) return MPHF_ETIMEOUT;
+    *out = r->out;
+    *status = r->status;
+    if (times) *times = r->t;
+    S->requests.erase(it);
+    delete r;
+    return MPHF_OK;
+}
+
+int mphf_server_destroy(mphf_server_t *S) {
+    if (!S) return MPHF_EINVAL;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    for (auto &t : S->workers) t.join();
+    for (auto st : S->streams) cudaStreamDestroy(st);
+    for (auto &kv : S->requests) {
+        if (kv.second->out) mphf_free(kv.second->out);
+        delete kv.second;
+    }
+    delete S;
+    return MPHF_OK;
 }
 
 }  // extern "C"

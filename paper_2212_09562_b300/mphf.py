@@ -69,6 +69,16 @@ class Stats(ctypes.Structure):
                 ("ms_pack", ctypes.c_float), ("ms_total", ctypes.c_float)]
 
 
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("executors", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("hbm_reserve_bytes", ctypes.c_uint64)]
+
+
+class RequestTimes(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("finished", ctypes.c_double)]
+
+
 class BuildDesc(ctypes.Structure):
     _fields_ = [("d_keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
                 ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
@@ -95,6 +105,10 @@ SIGNATURES = {
     "mphf_strerror": (ctypes.c_char_p, [_I]),
     "mphf_build_batch": (_I, [_P, _U32, _P, _P, _P]),
     "mphf_kernel_launches": (_U64, []),
+    "mphf_server_create": (_I, [_P, _P]),
+    "mphf_server_submit": (_I, [_P, _P, _P]),
+    "mphf_server_poll": (_I, [_P, _U64, _U32, _P, _P, _P]),
+    "mphf_server_destroy": (_I, [_P]),
 }
 
 
@@ -326,3 +340,50 @@ def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation: bool =
                 lib().mphf_free(ctypes.c_void_p(outs[i]))
         _check(rc, "mphf_build_batch")
     return [MPHF(outs[i]) for i in range(count)]
+
+
+class Server:
+    """Build server with continuous batching (mphf_server_*)."""
+
+    def __init__(self, executors: int = 2, max_batch: int = 64, hbm_reserve_bytes: int = 0):
+        _torch()
+        cfg = ServerCfg(executors, max_batch, hbm_reserve_bytes)
+        h = ctypes.c_void_p()
+        _check(lib().mphf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mphf_server_create")
+        self._h = h
+        self._keep = {}  # ticket -> key tensor, alive until the request is polled
+
+    def submit(self, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation: bool = True,
+               max_value: int = 0) -> int:
+        n, kb = key_layout(keys)
+        d = BuildDesc(keys.data_ptr() if n else None, n, leaf_size, bucket_size, kb,
+                      1 if rotation else 0, max_value)
+        t = ctypes.c_uint64()
+        _check(lib().mphf_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)),
+               "mphf_server_submit")
+        self._keep[t.value] = keys
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        """None if not finished; else (status, MPHF or None, (submitted, admitted, finished))."""
+        out, st, tm = ctypes.c_void_p(), ctypes.c_int(), RequestTimes()
+        rc = lib().mphf_server_poll(self._h, ticket, timeout_ms, ctypes.byref(out),
+                                    ctypes.byref(st), ctypes.byref(tm))
+        if rc == ETIMEOUT:
+            return None
+        _check(rc, "mphf_server_poll")
+        self._keep.pop(ticket, None)
+        built = MPHF(out.value) if out.value else None
+        return st.value, built, (tm.submitted, tm.admitted, tm.finished)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().mphf_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,131 @@
+"""Serving with continuous batching: every served result equals the plain
+build of the same request, alone or in a mix; admission follows arrival order
+under a memory budget; timeouts and bad requests are reported, not hung on."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2212_09562_b300 import mphf as M
+from paper_2212_09562_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2212_09562_b300 import build
+    build.build()
+    M.lib()
+    return t
+
+
+def dev(torch, keys):
+    return torch.from_numpy(keys.view(np.int64) if keys.ndim == 1 else np.ascontiguousarray(keys)).cuda()
+
+
+def same(a, b):
+    ha, hb = a.host_arrays(), b.host_arrays()
+    for k in ha:
+        assert np.array_equal(ha[k], hb[k]), k
+
+
+def requests(torch, count, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(10 ** rng.uniform(3, 4.6))
+        leaf = int(rng.choice([8, 12, 16]))
+        kb = int(rng.choice([8, 16]))
+        keys = W.random_keys(n, kb, seed * 100 + i)
+        out.append((dev(torch, keys), leaf))
+    return out
+
+
+def poll_all(srv, tickets, timeout_s=300):
+    res, t_end = {}, time.time() + timeout_s
+    while len(res) < len(tickets) and time.time() < t_end:
+        for t in tickets:
+            if t not in res:
+                r = srv.poll(t, 20)
+                if r is not None:
+                    res[t] = r
+    assert len(res) == len(tickets), "requests did not finish"
+    return res
+
+
+def test_served_results_equal_plain_builds(torch):
+    reqs = requests(torch, 16, 31)
+    srv = M.Server(executors=2, max_batch=8)
+    tickets = []
+
+    def arrive():  # staggered arrivals while earlier requests are on the device
+        for dk, leaf in reqs:
+            tickets.append(srv.submit(dk, leaf, 1000))
+            time.sleep(0.003)
+
+    th = threading.Thread(target=arrive)
+    th.start()
+    th.join()
+    res = poll_all(srv, tickets)
+    for t, (dk, leaf) in zip(tickets, reqs):
+        st, built, (ts, ta, tf) = res[t]
+        assert st == M.OK and built is not None
+        assert ts <= ta <= tf
+        same(built, M.MPHF.build(dk, leaf, 1000, True))
+        assert built.verify(dk) == 0
+    srv.close()
+
+
+def test_alone_equals_in_mix(torch):
+    reqs = requests(torch, 8, 32)
+    probe_keys, probe_leaf = reqs[3]
+    alone = M.Server(executors=1, max_batch=1)
+    t = alone.submit(probe_keys, probe_leaf, 500)
+    st, a, _ = poll_all(alone, [t])[t]
+    alone.close()
+    mix = M.Server(executors=2, max_batch=64)
+    tickets = [mix.submit(dk, leaf, 500) for dk, leaf in reqs]
+    res = poll_all(mix, tickets)
+    st2, b, _ = res[tickets[3]]
+    assert st == st2 == M.OK
+    same(a, b)
+    mix.close()
+
+
+def test_fifo_admission_under_a_memory_budget(torch):
+    free, _ = torch.cuda.mem_get_info()
+    reqs = requests(torch, 6, 33)
+    # reserve almost all free memory: only one request is admitted at a time
+    srv = M.Server(executors=2, max_batch=64, hbm_reserve_bytes=max(free - (64 << 20), 1))
+    tickets = [srv.submit(dk, leaf, 500) for dk, leaf in reqs]
+    res = poll_all(srv, tickets)
+    admitted = [res[t][2][1] for t in tickets]
+    assert admitted == sorted(admitted)
+    assert all(res[t][0] == M.OK for t in tickets)
+    srv.close()
+
+
+def test_timeout_and_bad_requests(torch):
+    keys = dev(torch, W.distinct_u64(300_000, 34))
+    srv = M.Server(executors=1)
+    t_big = srv.submit(keys, 16, 2000)
+    assert srv.poll(t_big, 0) is None  # still running: reported, not waited on
+    t_bad = srv.submit(keys, 1, 2000)  # leaf size out of range
+    res = poll_all(srv, [t_big, t_bad])
+    assert res[t_big][0] == M.OK
+    assert res[t_bad][0] == M.EINVAL and res[t_bad][1] is None
+    with pytest.raises(M.MPHFError):
+        srv.poll(123456, 0)
+    srv.close()
+
+
+def test_destroy_with_queued_requests(torch):
+    reqs = requests(torch, 6, 35)
+    srv = M.Server(executors=1, max_batch=2)
+    for dk, leaf in reqs:
+        srv.submit(dk, leaf, 500)
+    srv.close()  # finishes the queue, frees unpolled results
