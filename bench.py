@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the key count (profiling runs)")
+    ap.add_argument("--mode", choices=["build", "serve"], default="build")
+    ap.add_argument("--requests", type=int, default=24, help="serve mode: requests per run")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve mode: Poisson arrivals per second")
+    ap.add_argument("--batch-builds", type=int, default=128,
+                    help="builds in the batched-vs-plain comparison (0 = skip)")
     return ap.parse_args()
 
 
@@ -131,6 +136,97 @@ def cpu_baseline(w, keys, budget_s: float) -> dict:
     return {"value": sample_keys / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
             "sample": f"{count} of {nb} buckets ({sample_keys} keys) of {w.name}, seeded",
             "seconds": dt, "trials_per_s": trials / dt}
+
+
+def batch_vs_plain(M, torch, count: int) -> dict:
+    """The same independent builds (batch workload distribution, sizes 10^3..10^5)
+    through one batched call and through one call per build."""
+    inst = W.batch_instances(count=count, lo_exp=3.0, hi_exp=5.0)
+    keys = [torch.from_numpy(W.distinct_u64(x.n, x.seed).view(np.int64)).cuda() for x in inst]
+    leaves = [x.leaf for x in inst]
+    total = sum(x.n for x in inst)
+    for g in M.build_batch(keys[:4], leaves[:4], bucket_size=2000):
+        g.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batched = M.build_batch(keys, leaves, bucket_size=2000)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plain = [M.MPHF.build(k, l, 2000, True) for k, l in zip(keys, leaves)]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    identical = all(np.array_equal(a.host_arrays()["values"], b.host_arrays()["values"]) and
+                    np.array_equal(a.host_arrays()["gr"], b.host_arrays()["gr"])
+                    for a, b in zip(batched, plain))
+    for g in batched + plain:
+        g.close()
+    return {"builds": count, "keys": total, "sizes": "floor(10^U(3,5)), leaf in {8,12,16}, b=2000",
+            "batched_keys_per_s": total / t_batch, "plain_keys_per_s": total / t_plain,
+            "batched_over_plain": t_plain / t_batch, "identical": identical}
+
+
+def serve_run(M, torch, keys, leaf, arrivals) -> dict:
+    srv = M.Server(executors=2, max_batch=64)
+    tickets = []
+    start = time.perf_counter()
+    for dk, at in zip(keys, arrivals):
+        delay = at - (time.perf_counter() - start)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(dk, leaf, 2000))
+    res = {}
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t not in res:
+                r = srv.poll(t, 50)
+                if r is not None:
+                    res[t] = r
+    lat = sorted(r[2][2] - r[2][0] for r in res.values())
+    first = min(r[2][0] for r in res.values())
+    last = max(r[2][2] for r in res.values())
+    ok = all(r[0] == M.OK for r in res.values())
+    bad = sum(r[1].verify(dk) if r[1] is not None else 1
+              for r, dk in zip((res[t] for t in tickets), keys))
+    for r in res.values():
+        if r[1] is not None:
+            r[1].close()
+    srv.close()
+    n = sum(int(k.shape[0]) for k in keys)
+    return {"requests": len(keys), "keys": n, "keys_per_s": n / (last - first),
+            "requests_per_s": len(keys) / (last - first), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "all_ok": ok and bad == 0}
+
+
+def run_serve(args):
+    """Serve workload: Poisson arrivals of 16-byte-key builds, n = floor(10^U(4,7)),
+    l = 16, b = 2000; keys resident on the device before the clock starts."""
+    import torch
+    from paper_2212_09562_b300 import mphf as M
+    M.lib()
+    seed = W.SEED_BASE + 5
+    sizes = W.serve_sizes(args.requests, seed)
+    keys = [torch.from_numpy(W.distinct_bytes16(int(n), seed * 1000 + i)).cuda()
+            for i, n in enumerate(sizes)]
+    warm = M.Server(executors=1)
+    t = warm.submit(keys[0][:5000], 16, 2000)
+    while warm.poll(t, 100) is None:
+        pass
+    warm.close()
+    sampler = ClockSampler(0)
+    sampler.start()
+    offered = serve_run(M, torch, keys, 16, W.poisson_arrivals(args.requests, args.rate, seed))
+    rate2 = 0.8 * offered["requests_per_s"]
+    paced = serve_run(M, torch, keys, 16, W.poisson_arrivals(args.requests, rate2, seed + 1))
+    clocks = sampler.stop()
+    out = {"metric": "served MPHF build keys/s (l=16, b=2000, 16-byte keys, Poisson arrivals)",
+           "value": offered["keys_per_s"], "unit": "keys/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
+                      "sizes": "floor(10^U(4,7)) 16-byte keys", "executors": 2},
+           "offered_rate": offered, "paced_at_0.8x_capacity": dict(paced, rate_per_s=rate2),
+           "clocks": clocks}
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args):
@@ -264,6 +360,8 @@ def run_ours(args):
            "evals_per_s": world * evals / (total_ms / 1000.0),
            "search_ms": mean_search, "wall_s": wall,
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if world == 1 and args.batch_builds > 0:
+        out["batch"] = batch_vs_plain(M, torch, args.batch_builds)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, keys, args.cpu_seconds)
         out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
@@ -274,6 +372,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 
