@@ -255,6 +255,27 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def rank_keys(w, rank: int) -> np.ndarray:
+    """Each rank builds its own key set (weak scaling: independent builds)."""
+    return W.keys_for(w) if rank == 0 else W.random_keys(w.n, w.key_bytes, w.seed + rank)
+
+
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time decides the whole job's time."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, steps: int, n: int, total_ms: float) -> float:
+    """Keys built by all ranks per second of the slowest rank."""
+    return world * steps * n / (total_ms / 1000.0)
+
+
 def workload(args):
     w = W.WORKLOADS[args.workload]
     if args.n:
@@ -272,7 +293,7 @@ def run_ours(args):
     from paper_2212_09562_b300 import mphf as M
     M.lib()
     w = workload(args)
-    keys = W.random_keys(w.n, w.key_bytes, w.seed + rank) if rank else W.keys_for(w)
+    keys = rank_keys(w, rank)
     dkeys = torch.from_numpy(keys.view(np.int64) if keys.ndim == 1 else keys).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     stream = torch.cuda.current_stream()
@@ -312,13 +333,8 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall
     launches = M.kernel_launches() - launches0 - 3  # minus the final verify's query/mark/memset-free
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    keys_per_s = world * args.steps * w.n / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    keys_per_s = weak_scaling_value(world, args.steps, w.n, total_ms)
 
     # end to end through the public host-buffer call: pinned keys in, packed function out
     e2e = None

@@ -197,8 +197,12 @@ class MPHF:
     @classmethod
     def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation: bool = True,
               max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
-              blocks_per_sm: int = 0, stream=None) -> "MPHF":
+              blocks_per_sm: int = 0, stream=None, tuned: bool = False) -> "MPHF":
+        """tuned=True takes the launch shape from the autotuner's cache."""
         n, kb = key_layout(keys)
+        if tuned and not threads_per_block and not blocks_per_sm:
+            from .autotune import tuned as cached_shape
+            threads_per_block, blocks_per_sm = cached_shape(leaf_size, rotation)
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
         p.rotation_fitting = 1 if rotation else 0
