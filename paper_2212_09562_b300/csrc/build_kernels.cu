@@ -385,26 +385,46 @@ __device__ __forceinline__ ModCTR<MM> make_modct(uint32_t c_from_memory) {
 // (2^w - 1) < 0 keys (p_last <= unit <= 2^w - 2).
 // The whole chunk of seeds is decided before the next one starts, so the
 // smallest working seed wins.
+#ifndef MPHF_UNROLL
+#define MPHF_UNROLL 8
+#endif
+#ifndef MPHF_PAIRS
+#define MPHF_PAIRS 1
+#endif
+constexpr int kKeyUnroll = MPHF_UNROLL;  // key-loop unroll factor of the split search
+
 template <class Cnt, class Mod, class Div>
-__device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div, const Cnt *lut,
-                                 Cnt expected, const Mixer &mx, uint64_t maxv, bool &limit,
-                                 BlockState &S) {
+__device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div,
+                                                 const Cnt *lut, Cnt expected, const Mixer &mx,
+                                                 uint64_t maxv, bool &limit, BlockState &S) {
     const uint32_t T = blockDim.x;
     for (uint64_t base = 0;; base += (uint64_t)T * MPHF_SPT) {
         Cnt cnt[MPHF_SPT];
 #pragma unroll
         for (int j = 0; j < MPHF_SPT; j++) cnt[j] = 0;
         const uint64_t s0 = base + threadIdx.x;
-#pragma unroll 4
-        for (uint32_t i = 0; i < m; i++) {
-            const uint64_t x = xs[i];
+        auto eval = [&](uint64_t x) {
 #pragma unroll
             for (int j = 0; j < MPHF_SPT; j++) {
                 uint32_t hl, hh;
                 mx(x + s0 + (uint64_t)j * T, hl, hh);
                 cnt[j] += lut[div(mod_halves(mod, hl, hh))];
             }
+        };
+#if MPHF_PAIRS
+        // xs is 16-byte aligned: two keys per shared-memory load
+        const ulonglong2 *xs2 = (const ulonglong2 *)xs;
+#pragma unroll kKeyUnroll
+        for (uint32_t i = 0; i < m / 2; i++) {
+            const ulonglong2 q = xs2[i];
+            eval(q.x);
+            eval(q.y);
         }
+        if (m & 1) eval(xs[m - 1]);
+#else
+#pragma unroll kKeyUnroll
+        for (uint32_t i = 0; i < m; i++) eval(xs[i]);
+#endif
         uint64_t best = ~0ull;
 #pragma unroll
         for (int j = MPHF_SPT - 1; j >= 0; j--)
@@ -539,10 +559,11 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
     const uint32_t T = blockDim.x, tid = threadIdx.x;
     const uint32_t kind = node_kind(sh, m);
     const uint64_t salt = level_salt(salt_level(sh, m, depth));
-    for (uint32_t i = tid; i < m; i += T) A.tlo[off + i] = A.lo[off + i] + salt;
+    // salted keys of the node at the start of the (16-byte aligned) scratch area
+    for (uint32_t i = tid; i < m; i += T) A.tlo[i] = A.lo[off + i] + salt;
     if (tid == 0) S.found = ~0ull;
     __syncthreads();
-    const uint64_t *xs = A.tlo + off;
+    const uint64_t *xs = A.tlo;
     const uint32_t np = num_parts(sh, m);
     uint64_t x = 0;
     bool limit = false;
