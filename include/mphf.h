@@ -70,7 +70,17 @@ typedef struct {
  *                    more fails the build with MPHF_ESEARCH_LIMIT.
  *   threads_per_block, blocks_per_sm
  *                    launch shape of the search kernel; 0 = the tuned or
- *                    default choice. */
+ *                    default choice.
+ *   leaf_method      how leaves are searched (same result every time):
+ *                    MPHF_LEAF_LOCKSTEP  every trial hashes all m keys
+ *                                        (default, the fastest measured);
+ *                    MPHF_LEAF_EARLY     a trial stops at its first collision;
+ *                    MPHF_LEAF_TABLE     as EARLY, the rotation from a table of
+ *                                        canonical rotations (leaves of <= 16
+ *                                        keys; Section 4, "Lookup Tables"). */
+#define MPHF_LEAF_LOCKSTEP 0u
+#define MPHF_LEAF_EARLY 1u
+#define MPHF_LEAF_TABLE 2u
 typedef struct {
     uint32_t leaf_size;
     uint32_t bucket_size;
@@ -80,6 +90,8 @@ typedef struct {
     const mphf_allocator *allocator;
     uint32_t threads_per_block;
     uint32_t blocks_per_sm;
+    uint32_t leaf_method;
+    uint32_t reserved;
 } mphf_build_params;
 
 /* Sizes and parameters of a built function. */
@@ -108,7 +120,8 @@ typedef struct {
 } mphf_stats;
 
 /* Fills *p with leaf 16, bucket 2000, 8-byte keys, rotation fitting on,
- * max_value MPHF_DEFAULT_MAX_VALUE, default allocator and launch shape. */
+ * max_value MPHF_DEFAULT_MAX_VALUE, default allocator and launch shape,
+ * MPHF_LEAF_LOCKSTEP leaves. */
 void mphf_default_params(mphf_build_params *p);
 
 /* Builds the function of the n keys at d_keys (Section 2.2, the whole

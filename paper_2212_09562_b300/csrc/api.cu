@@ -63,6 +63,51 @@ int device_tables(int dev, uint32_t leaf, uint32_t rotation, DevTables *out) {
     return MPHF_OK;
 }
 
+// Rotation tables for leaves of m <= 16 keys, all m in one array (m's table
+// at offset 2^m - 4): canonical rotation (the smallest r giving the smallest
+// rot_m^r(x)) and rotation period of every m-bit word.  Per device, kept.
+int device_rot_tables(int dev, const uint8_t **canon, const uint8_t **period) {
+    static std::mutex mu;
+    static std::map<int, std::pair<uint8_t *, uint8_t *>> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) {
+        *canon = it->second.first;
+        *period = it->second.second;
+        return MPHF_OK;
+    }
+    const size_t total = (1u << 17) - 4;  // sum over m = 2..16 of 2^m
+    std::vector<uint8_t> c(total), pr(total);
+    for (uint32_t m = 2; m <= 16; m++) {
+        const uint32_t full = (1u << m) - 1, base = (1u << m) - 4;
+        for (uint32_t x = 0; x <= full; x++) {
+            uint32_t best = x, br = 0, per = m;
+            for (uint32_t r = 1; r < m; r++) {
+                uint32_t y = ((x << r) | (x >> (m - r))) & full;
+                if (y < best) {
+                    best = y;
+                    br = r;
+                }
+                if (y == x && per == m) per = r;
+            }
+            c[base + x] = (uint8_t)br;
+            pr[base + x] = (uint8_t)per;
+        }
+    }
+    uint8_t *dc = nullptr, *dp = nullptr;
+    if (cudaMalloc(&dc, total) != cudaSuccess || cudaMalloc(&dp, total) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ENOMEM;
+    }
+    if (cudaMemcpy(dc, c.data(), total, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dp, pr.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+        return MPHF_ECUDA;
+    cache[dev] = {dc, dp};
+    *canon = dc;
+    *period = dp;
+    return MPHF_OK;
+}
+
 struct Mem {
     const mphf_allocator *a;
     cudaStream_t st;
@@ -143,6 +188,7 @@ void mphf_default_params(mphf_build_params *p) {
     p->key_bytes = 8;
     p->rotation_fitting = 1;
     p->max_value = MPHF_DEFAULT_MAX_VALUE;
+    p->leaf_method = MPHF_LEAF_LOCKSTEP;
 }
 
 const char *mphf_strerror(int code) {
@@ -201,6 +247,7 @@ int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
     if (p->threads_per_block &&
         (p->threads_per_block % 32 || p->threads_per_block > 512 || p->threads_per_block < 64))
         return MPHF_EINVAL;
+    if (p->leaf_method > MPHF_LEAF_TABLE) return MPHF_EINVAL;
     return MPHF_OK;
 }
 
@@ -351,6 +398,13 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         d.red[0] = (uint32_t)((1ull << 32) % j.p.leaf_size);
         d.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
         d.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
+        d.leaf_method = j.p.leaf_method;
+        d.rot_canon = d.rot_period = nullptr;
+        if (j.p.leaf_method == MPHF_LEAF_TABLE &&
+            device_rot_tables(h->device, &d.rot_canon, &d.rot_period) != MPHF_OK) {
+            fail_job(j, MPHF_ENOMEM, mem);
+            continue;
+        }
         inst_job.push_back((uint32_t)i);
         hinst.push_back(d);
         total_items += j.nb;

@@ -540,6 +540,98 @@ __device__ __forceinline__ uint64_t leaf_rotation(const uint64_t *xs, const uint
     }
 }
 
+// Leaf search with early rejection (the early-exit brute force that the
+// paper's hash-evaluation counts of Appendix C assume).  Lane L tries its own
+// trials L, L + 32, L + 64, ... (seed t for plain leaves, t*m for rotation
+// fitting).  All lanes walk the leaf's keys cyclically in lock step, so every
+// key load is a broadcast; a lane abandons a trial at its first collision
+// (within A or within B for rotation fitting) and starts its next trial at the
+// next key.  A trial that places all m keys without collision is a bijection
+// (plain) or leaves only the rotation to find (Section 4).  A lane stops after
+// its first candidate or once its trials cannot beat the warp's best value, so
+// the warp's minimum is the smallest stored value, as with the lock-step form.
+// With a lookup table (m <= 16) the rotation comes from canonical rotations:
+// r = (t[~b] - t[a]) mod m, reduced modulo the period of ~b to the smallest
+// working rotation (Section 4, "Lookup Tables").
+template <bool ROT, class Mod>
+__device__ __forceinline__ uint64_t leaf_cyclic(const uint64_t *xs, const uint8_t *bbs, uint32_t m,
+                                                Mod mod, const Mixer &mx, uint64_t maxv,
+                                                bool &limit, uint32_t lane,
+                                                const uint8_t *canon, const uint8_t *period) {
+    const uint32_t full = (1u << m) - 1;
+    const uint64_t step = ROT ? m : 1;
+    uint64_t t = lane;  // this lane's current trial
+    uint32_t a = 0, b = 0, prog = 0;
+    uint64_t best = ~0ull;  // warp-uniform
+    bool active = true;
+    uint32_t i = 0;  // warp-uniform key index
+    for (;;) {
+        if (active && (t * step > best || t * step > maxv)) active = false;
+        if (!__any_sync(0xffffffffu, active)) break;
+        uint64_t cand = ~0ull;
+        if (active) {
+            uint32_t hl, hh;
+            mx(xs[i] + t * step, hl, hh);
+            const uint32_t bit = 1u << mod_halves(mod, hl, hh);
+            bool coll;
+            if (ROT && bbs[i]) {
+                coll = (b & bit) != 0;
+                b |= bit;
+            } else {
+                coll = (a & bit) != 0;
+                a |= bit;
+            }
+            if (coll) {
+                t += 32;
+                a = b = 0;
+                prog = 0;
+            } else if (++prog == m) {
+                if (!ROT) {
+                    cand = t;
+                    active = false;
+                } else {
+                    int rf = -1;
+                    if (canon) {
+                        const uint32_t nb_ = ~b & full;
+                        uint32_t r = (canon[nb_] + m - canon[a]) % m;
+                        r %= period[nb_];
+                        const uint32_t rot = r == 0 ? b : (((b << r) | (b >> (m - r))) & full);
+                        if ((a | rot) == full) rf = (int)r;
+                    } else {
+                        for (uint32_t r = 0; r < m; r++) {
+                            const uint32_t rot = r == 0 ? b : (((b << r) | (b >> (m - r))) & full);
+                            if ((a | rot) == full) {
+                                rf = (int)r;
+                                break;
+                            }
+                        }
+                    }
+                    if (rf >= 0) {
+                        cand = t * m + (uint32_t)rf;
+                        active = false;
+                    } else {
+                        t += 32;
+                        a = b = 0;
+                        prog = 0;
+                    }
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, cand != ~0ull)) {
+            uint64_t c = cand;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, c, o);
+                c = y < c ? y : c;
+            }
+            best = c < best ? c : best;
+        }
+        i = i + 1 == m ? 0 : i + 1;
+    }
+    if (best > maxv) limit = true;
+    return best;
+}
+
 // Any two equal lo words among keys [0, m) of the block's bucket.
 __device__ __forceinline__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
     bool dup = false;
@@ -691,16 +783,32 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
         bool limit = false;
         uint64_t x;
         bool done = false;
-        if constexpr (LEAF != 0) {
-            if (m == (uint32_t)LEAF) {  // full leaf: compile-time modulus
-                x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
-                               : leaf_plain(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
-                done = true;
+        if (d.leaf_method == 0) {  // lock-step: every lane hashes all m keys per trial
+            if constexpr (LEAF != 0) {
+                if (m == (uint32_t)LEAF) {  // full leaf: compile-time modulus
+                    x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
+                                   : leaf_plain(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
+                    done = true;
+                }
             }
+            if (!done)
+                x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane)
+                               : leaf_plain(xs, m, make_mod(m), mx, d.max_value, limit, lane);
+        } else {  // early rejection (1), with the rotation lookup table (2)
+            const bool use_lut = d.leaf_method == 2 && m <= 16 && d.rot_canon;
+            const uint8_t *canon = use_lut ? d.rot_canon + ((1u << m) - 4) : nullptr;
+            const uint8_t *period = use_lut ? d.rot_period + ((1u << m) - 4) : nullptr;
+            if constexpr (LEAF != 0) {
+                if (m == (uint32_t)LEAF) {
+                    x = d.rotation ? leaf_cyclic<true>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, canon, period)
+                                   : leaf_cyclic<false>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, nullptr, nullptr);
+                    done = true;
+                }
+            }
+            if (!done)
+                x = d.rotation ? leaf_cyclic<true>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, canon, period)
+                               : leaf_cyclic<false>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, nullptr, nullptr);
         }
-        if (!done)
-            x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane)
-                           : leaf_plain(xs, m, make_mod(m), mx, d.max_value, limit, lane);
         if (lane == 0) {
             if (limit) {
                 atomicOr(&S.flags, ST_LIMIT);

@@ -24,6 +24,9 @@ struct InstDesc {
     uint32_t nb;
     uint32_t k30, k27, k31;      // 4, 32, 2: multipliers of the hash's xor-shifts
     uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
+    uint32_t leaf_method;        // 0 lock-step, 1 early rejection, 2 early rejection + table
+    const uint8_t *rot_canon;    // per m <= 16 at offset 2^m - 4: canonical rotation of x
+    const uint8_t *rot_period;   // same layout: rotation period of x
 };
 
 // One unit of work: a bucket of an instance (inst = all ones: an empty slot).

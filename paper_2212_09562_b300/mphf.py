@@ -30,6 +30,7 @@ ETIMEOUT = -9
 MAX_BUCKET = 4096
 VERIFY_STATIC_MAX_KEYS = 1 << 20
 DEFAULT_MAX_VALUE = (1 << 40) - 1
+LEAF_LOCKSTEP, LEAF_EARLY, LEAF_TABLE = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -50,7 +51,8 @@ class BuildParams(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_uint32), ("bucket_size", ctypes.c_uint32),
                 ("key_bytes", ctypes.c_uint32), ("rotation_fitting", ctypes.c_uint32),
                 ("max_value", ctypes.c_uint64), ("allocator", ctypes.c_void_p),
-                ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+                ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("leaf_method", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Info(ctypes.Structure):
@@ -197,8 +199,10 @@ class MPHF:
     @classmethod
     def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation: bool = True,
               max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
-              blocks_per_sm: int = 0, stream=None, tuned: bool = False) -> "MPHF":
-        """tuned=True takes the launch shape from the autotuner's cache."""
+              blocks_per_sm: int = 0, stream=None, tuned: bool = False,
+              leaf_method: int | None = None) -> "MPHF":
+        """tuned=True takes the launch shape from the autotuner's cache;
+        leaf_method: LEAF_LOCKSTEP (default), LEAF_EARLY or LEAF_TABLE."""
         n, kb = key_layout(keys)
         if tuned and not threads_per_block and not blocks_per_sm:
             from .autotune import tuned as cached_shape
@@ -208,6 +212,8 @@ class MPHF:
         p.rotation_fitting = 1 if rotation else 0
         p.max_value = max_value
         p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
+        if leaf_method is not None:
+            p.leaf_method = leaf_method
         h = ctypes.c_void_p()
         rc = lib().mphf_build_ex(keys.data_ptr() if n else None, n, ctypes.byref(p),
                                  _stream(stream), ctypes.byref(h))
