@@ -113,6 +113,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def bucket_index(hi: np.ndarray, nb: int) -> np.ndarray:
+    """floor(hi * nb / 2^64) exactly, on 32-bit halves (nb < 2^32)."""
+    h, l = hi >> np.uint64(32), hi & np.uint64(0xFFFFFFFF)
+    nbu = np.uint64(nb)
+    return ((h * nbu + ((l * nbu) >> np.uint64(32))) >> np.uint64(32)).astype(np.int64)
+
+
 def cpu_baseline(w, keys, budget_s: float) -> dict:
     """The oracle as it stands, on all host cores, on a bounded bucket sample."""
     from oracle import oracle as O
@@ -124,14 +131,13 @@ def cpu_baseline(w, keys, budget_s: float) -> dict:
     O.build_sample(keys, w.leaf, w.bucket, w.rotation, probe, threads=1)
     one = time.perf_counter() - t0
     count = int(max(1, min(nb, round(budget_s * cores / max(one, 1e-3)))))
-    count = max(cores, count - count % cores) if count >= cores else count
+    count = min(nb, max(cores, count - count % cores))  # at least one bucket per core
     sample = W.sample_buckets(nb, count, w.seed + 100)
     t0 = time.perf_counter()
     vals, counts, st = O.build_sample(keys, w.leaf, w.bucket, w.rotation, sample, threads=cores)
     dt = time.perf_counter() - t0
     hi, _ = O.fingerprint(keys)
-    b = (hi.astype(object) * nb >> 64).astype(np.int64)
-    sample_keys = int(np.isin(b, sample.astype(np.int64)).sum())
+    sample_keys = int(np.isin(bucket_index(hi, nb), sample.astype(np.int64)).sum())
     trials = sum(v[0] for v in st.values())
     return {"value": sample_keys / dt, "unit": "keys/s", "cores": cores, "kind": "oracle",
             "sample": f"{count} of {nb} buckets ({sample_keys} keys) of {w.name}, seeded",
@@ -255,6 +261,21 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def query_throughput(torch, g, dkeys, stream, reps: int = 5) -> dict:
+    """Queries of every built key through mphf_query, keys and results on the device."""
+    out = torch.empty(dkeys.shape[0], dtype=torch.int64, device="cuda")
+    g.query(dkeys, out=out)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        g.query(dkeys, out=out)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    return {"keys": int(dkeys.shape[0]), "ms": ms, "queries_per_s": dkeys.shape[0] / (ms / 1000.0)}
+
+
 def rank_keys(w, rank: int) -> np.ndarray:
     """Each rank builds its own key set (weak scaling: independent builds)."""
     return W.keys_for(w) if rank == 0 else W.random_keys(w.n, w.key_bytes, w.seed + rank)
@@ -328,6 +349,8 @@ def run_ours(args):
         if i == args.steps - 1:
             bad = g.verify(dkeys)
             assert bad == 0, f"built function is not a bijection ({bad} bad keys)"
+            stages = st["ms"]
+            query = query_throughput(torch, g, dkeys, stream)
         g.close()
     barrier()
     wall = time.perf_counter() - t_wall
@@ -374,7 +397,7 @@ def run_ours(args):
                       "parallelism": f"{world} independent builds (one per GPU)"},
            "trials_per_s": world * trials / (total_ms / 1000.0),
            "evals_per_s": world * evals / (total_ms / 1000.0),
-           "search_ms": mean_search, "wall_s": wall,
+           "search_ms": mean_search, "wall_s": wall, "stage_ms": stages, "query": query,
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if world == 1 and args.batch_builds > 0:
         out["batch"] = batch_vs_plain(M, torch, args.batch_builds)

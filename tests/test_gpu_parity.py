@@ -191,7 +191,9 @@ def _sampled_parity(torch, orc, name, count):
         off += int(c)
     # bucket sizes equal the oracle's recount; the whole function is a bijection
     hi, _ = orc.fingerprint(keys)
-    counts_all = np.bincount((hi.astype(object) * nb >> 64).astype(np.int64), minlength=nb)
+    h, l = hi >> np.uint64(32), hi & np.uint64(0xFFFFFFFF)
+    bidx = ((h * np.uint64(nb) + ((l * np.uint64(nb)) >> np.uint64(32))) >> np.uint64(32)).astype(np.int64)
+    counts_all = np.bincount(bidx, minlength=nb)
     assert np.array_equal(np.diff(a["cum_keys"]).astype(np.int64), counts_all)
     assert g.verify(dkeys) == 0
     return g
