@@ -234,6 +234,8 @@ struct Job {
     uint64_t *lo_s = nullptr, *counters = nullptr;
     uint8_t *bb_s = nullptr;
     uint32_t *cursor = nullptr, *small = nullptr;  // small: status, max bucket, spare
+    uint32_t *blk = nullptr;                         // per-block bucket counts (two-level sort)
+    uint32_t sort_g = 0;
     uint16_t *node_m = nullptr;
     uint64_t n_nodes = 0;
 };
@@ -258,6 +260,8 @@ void free_job_scratch(Job &j, Mem &mem) {
     mem.put(j.small);
     mem.put(j.node_m);
     mem.put(j.counters);
+    mem.put(j.blk);
+    j.blk = nullptr;
     j.lo_s = j.counters = nullptr;
     j.bb_s = nullptr;
     j.cursor = j.small = nullptr;
@@ -328,8 +332,10 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         j.lo_s = (uint64_t *)mem.get(j.n * 8);
         j.bb_s = (uint8_t *)mem.get(j.n);
         j.counters = (uint64_t *)mem.get(64);
+        j.sort_g = sort_blocks(j.n, nb);
+        if (j.sort_g) j.blk = (uint32_t *)mem.get((uint64_t)j.sort_g * nb * 4);
         if (!h->cum_keys || !h->node_off || !h->bit_pos || !j.cursor || !j.small || !j.lo_s ||
-            !j.bb_s || !j.counters) {
+            !j.bb_s || !j.counters || (j.sort_g && !j.blk)) {
             fail_job(j, MPHF_ENOMEM, mem);
             continue;
         }
@@ -338,7 +344,10 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         CU(cudaMemsetAsync(j.cursor, 0, (nb + 1) * 4, st));
         CU(cudaMemsetAsync(j.small, 0, 64, st));
         CU(cudaMemsetAsync(j.counters, 0, 64, st));
-        launch_fp_hist(j.d_keys, j.n, j.p.key_bytes, nb, h->cum_keys, st);
+        if (j.sort_g)
+            launch_fp_hist_blk(j.d_keys, j.n, j.p.key_bytes, nb, j.sort_g, h->cum_keys, j.blk, st);
+        else
+            launch_fp_hist(j.d_keys, j.n, j.p.key_bytes, nb, h->cum_keys, st);
         launch_plan(h->cum_keys, nb, h->tabs.nodes, h->node_off, j.small, j.small + 1, size_hist, st);
         launch_exclusive_scan(h->cum_keys, nb + 1, scan_tmp, st);
         launch_exclusive_scan(h->node_off, nb + 1, scan_tmp, st);
@@ -376,7 +385,12 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
             fail_job(j, MPHF_ENOMEM, mem);
             continue;
         }
-        launch_scatter(j.d_keys, j.n, j.p.key_bytes, j.nb, h->cum_keys, j.cursor, j.lo_s, j.bb_s, st);
+        if (j.sort_g)
+            launch_scatter_blk(j.d_keys, j.n, j.p.key_bytes, j.nb, j.sort_g, h->cum_keys, j.blk,
+                               j.lo_s, j.bb_s, st);
+        else
+            launch_scatter(j.d_keys, j.n, j.p.key_bytes, j.nb, h->cum_keys, j.cursor, j.lo_s,
+                           j.bb_s, st);
         InstDesc d;
         memset(&d, 0, sizeof(d));
         d.lo = j.lo_s;

@@ -67,6 +67,101 @@ void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 }
 
 // ---------------------------------------------------------------------------
+// Two-level counting sort for builds with few buckets (nb <= kSmemBuckets):
+// block g takes the contiguous chunk [g*C, (g+1)*C) of keys, counts its
+// buckets in shared memory, and writes its counts as row g of blk[G][nb]
+// (plus one global add per bucket for the totals).  A column pass turns row g
+// into the block's first slot in every bucket, and the scatter re-reads the
+// chunk and places keys through shared-memory cursors.  Global atomics drop
+// from one per key to one per bucket and block.
+constexpr uint32_t kSmemBuckets = 8192;
+
+__global__ void k_fp_hist_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb,
+                              uint64_t chunk, unsigned long long *counts, uint32_t *blk) {
+    extern __shared__ uint32_t hist[];
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+    for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        uint64_t w0, w1, hi, lo;
+        load_key(keys, i, kb, w0, w1);
+        fingerprint(w0, w1, hi, lo);
+        atomicAdd(&hist[mulhi64(hi, nb)], 1u);
+    }
+    __syncthreads();
+    uint32_t *row = blk + (uint64_t)blockIdx.x * nb;
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+        const uint32_t c = hist[b];
+        row[b] = c;
+        if (c) atomicAdd(&counts[b], (unsigned long long)c);
+    }
+}
+
+// blk[g][b] <- bucket_off[b] + sum of blk[g'][b] over g' < g: one warp per
+// bucket, 32 rows at a time with a shuffle scan (the column is L2-resident).
+__global__ void k_block_offsets(uint32_t *blk, uint32_t G, uint32_t nb, const uint64_t *bucket_off) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t b = warp; b < nb; b += nwarps) {
+        uint32_t run = (uint32_t)bucket_off[b];
+        for (uint32_t g0 = 0; g0 < G; g0 += 32) {
+            const uint32_t g = g0 + lane;
+            const uint32_t v = g < G ? blk[(uint64_t)g * nb + b] : 0;
+            uint32_t incl = v;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= (uint32_t)d) incl += o;
+            }
+            if (g < G) blk[(uint64_t)g * nb + b] = run + incl - v;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+__global__ void k_scatter_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb, uint64_t chunk,
+                              const uint32_t *blk, uint64_t *lo_out, uint8_t *bb_out) {
+    extern __shared__ uint32_t cursor[];
+    const uint32_t *row = blk + (uint64_t)blockIdx.x * nb;
+    for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cursor[b] = row[b];
+    __syncthreads();
+    const uint64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+    for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        uint64_t w0, w1, hi, lo;
+        load_key(keys, i, kb, w0, w1);
+        fingerprint(w0, w1, hi, lo);
+        const uint32_t p = atomicAdd(&cursor[mulhi64(hi, nb)], 1u);
+        lo_out[p] = lo;
+        bb_out[p] = (uint8_t)(hi & 1);
+    }
+}
+
+uint32_t sort_blocks(uint64_t n, uint64_t nb) {
+    if (nb == 0 || nb > kSmemBuckets || n < 4096) return 0;  // use the global-atomic path
+    uint64_t g = (n + 8191) / 8192;                          // at least 8192 keys per block
+    return (uint32_t)(g > 2 * 148 ? 2 * 148 : g);
+}
+
+void launch_fp_hist_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                        uint32_t G, uint64_t *counts, uint32_t *blk, cudaStream_t st) {
+    const uint64_t chunk = (n + G - 1) / G;
+    k_fp_hist_blk<<<G, 512, (uint32_t)nb * 4, st>>>(keys, n, key_bytes, (uint32_t)nb, chunk,
+                                                    (unsigned long long *)counts, blk);
+    note_launches(1);
+}
+
+void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint32_t G,
+                        const uint64_t *bucket_off, uint32_t *blk, uint64_t *lo, uint8_t *bb,
+                        cudaStream_t st) {
+    const uint64_t chunk = (n + G - 1) / G;
+    k_block_offsets<<<(uint32_t)((nb * 32 + 255) / 256), 256, 0, st>>>(blk, G, (uint32_t)nb, bucket_off);
+    note_launches(1);
+    k_scatter_blk<<<G, 512, (uint32_t)nb * 4, st>>>(keys, n, key_bytes, (uint32_t)nb, chunk, blk, lo, bb);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
 // Plan: nodes per bucket, oversized buckets, largest bucket, and a histogram
 // of bucket sizes in descending order (size_hist[4096 - m]) for the work order.
 __global__ void k_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab,
@@ -282,9 +377,6 @@ struct DivRT {
 #ifndef MPHF_RTC
 #define MPHF_RTC 1
 #endif
-#ifndef MPHF_SPT
-#define MPHF_SPT 1
-#endif
 
 __device__ __forceinline__ void xorshift_mul(uint32_t &zl, uint32_t &zh, uint32_t k) {
     uint32_t a, b, c;
@@ -393,19 +485,22 @@ __device__ __forceinline__ ModCTR<MM> make_modct(uint32_t c_from_memory) {
 #endif
 constexpr int kKeyUnroll = MPHF_UNROLL;  // key-loop unroll factor of the split search
 
-template <class Cnt, class Mod, class Div>
+// SPT seeds per thread and round: two independent hash chains per key load
+// pay off where trials are many (the full nodes of l = 16); one keeps the
+// round (and the work past the winning seed) small elsewhere.
+template <int SPT, class Cnt, class Mod, class Div>
 __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div,
                                                  const Cnt *lut, Cnt expected, const Mixer &mx,
                                                  uint64_t maxv, bool &limit, BlockState &S) {
     const uint32_t T = blockDim.x;
-    for (uint64_t base = 0;; base += (uint64_t)T * MPHF_SPT) {
-        Cnt cnt[MPHF_SPT];
+    for (uint64_t base = 0;; base += (uint64_t)T * SPT) {
+        Cnt cnt[SPT];
 #pragma unroll
-        for (int j = 0; j < MPHF_SPT; j++) cnt[j] = 0;
+        for (int j = 0; j < SPT; j++) cnt[j] = 0;
         const uint64_t s0 = base + threadIdx.x;
         auto eval = [&](uint64_t x) {
 #pragma unroll
-            for (int j = 0; j < MPHF_SPT; j++) {
+            for (int j = 0; j < SPT; j++) {
                 uint32_t hl, hh;
                 mx(x + s0 + (uint64_t)j * T, hl, hh);
                 cnt[j] += lut[div(mod_halves(mod, hl, hh))];
@@ -427,7 +522,7 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
 #endif
         uint64_t best = ~0ull;
 #pragma unroll
-        for (int j = MPHF_SPT - 1; j >= 0; j--)
+        for (int j = SPT - 1; j >= 0; j--)
             if (cnt[j] == expected && s0 + (uint64_t)j * T <= maxv) best = s0 + (uint64_t)j * T;
         const bool ok = best != ~0ull;
         if (__syncthreads_or(ok)) {
@@ -435,7 +530,7 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
             __syncthreads();
             return S.found;
         }
-        if (base + (uint64_t)T * MPHF_SPT > maxv) {
+        if (base + (uint64_t)T * SPT > maxv) {
             limit = true;
             return 0;
         }
@@ -470,14 +565,19 @@ __device__ __forceinline__ uint64_t search_upper(const uint64_t *xs, uint32_t m,
 }
 
 // Leaf, plain brute force (Section 2.2 "Bijections"): one warp, lane = seed.
-template <class Mod>
-__device__ __forceinline__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, Mod mod, const Mixer &mx,
-                               uint64_t maxv, bool &limit, uint32_t lane) {
+// MT = m known at compile time (full leaves: the key loop unrolls), 0 = runtime m.
+template <uint32_t MT, class Mod>
+__device__ __forceinline__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m_rt, Mod mod,
+                                               const Mixer &mx, uint64_t maxv, bool &limit,
+                                               uint32_t lane) {
+    const uint32_t m = MT ? MT : m_rt;
     const uint32_t full = (1u << m) - 1;
     for (uint64_t s0 = 0;; s0 += 32) {
         uint64_t s = s0 + lane;
         uint32_t mask = 0;
-        for (uint32_t i = 0; i < m; i++) {
+#pragma unroll
+        for (uint32_t i = 0; i < (MT ? MT : 32u); i++) {
+            if (!MT && i >= m) break;
             uint32_t hl, hh;
             mx(xs[i] + s, hl, hh);
             mask |= 1u << mod_halves(mod, hl, hh);
@@ -498,21 +598,25 @@ __device__ __forceinline__ uint64_t leaf_plain(const uint64_t *xs, uint32_t m, M
 // Leaf with rotation fitting (Section 4): lane = k, seed k*m; keys of A set
 // bits of a, keys of B bits of b; the smallest r with a | rot_m^r(b) full.
 // The lowest lane with a hit has the smallest k, hence the smallest k*m + r.
-template <class Mod>
-__device__ __forceinline__ uint64_t leaf_rotation(const uint64_t *xs, const uint8_t *bbs, uint32_t m, Mod mod,
-                                  const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
+// bmask has bit i set for the keys of B.
+template <uint32_t MT, class Mod>
+__device__ __forceinline__ uint64_t leaf_rotation(const uint64_t *xs, uint32_t bmask, uint32_t m_rt,
+                                                  Mod mod, const Mixer &mx, uint64_t maxv,
+                                                  bool &limit, uint32_t lane) {
+    const uint32_t m = MT ? MT : m_rt;
     const uint32_t full = (1u << m) - 1;
-    uint32_t nb = 0;
-    for (uint32_t i = 0; i < m; i++) nb += bbs[i];
+    const uint32_t nb = __popc(bmask);
     const uint32_t na = m - nb;
     for (uint64_t k0 = 0;; k0 += 32) {
         uint64_t s = (k0 + lane) * m;
         uint32_t a = 0, b = 0;
-        for (uint32_t i = 0; i < m; i++) {
+#pragma unroll
+        for (uint32_t i = 0; i < (MT ? MT : 32u); i++) {
+            if (!MT && i >= m) break;
             uint32_t hl, hh;
             mx(xs[i] + s, hl, hh);
             uint32_t bit = 1u << mod_halves(mod, hl, hh);
-            if (bbs[i])
+            if ((bmask >> i) & 1)
                 b |= bit;
             else
                 a |= bit;
@@ -686,12 +790,12 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
             if (m == L1) {
                 const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
-                x = search_lower<C1>(xs, m, make_modct<L1>(d.red[1]), DivCT<LEAF>(), lut, (C1)expected, mx,
+                x = search_lower<(LEAF >= 16 ? 2 : 1), C1>(xs, m, make_modct<L1>(d.red[1]), DivCT<LEAF>(), lut, (C1)expected, mx,
                                      d.max_value, limit, S);
                 done = true;
             } else if (m == L2) {
                 const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
-                x = search_lower<C2>(xs, m, make_modct<L2>(d.red[2]), DivCT<L1>(), lut, (C2)expected, mx,
+                x = search_lower<(LEAF >= 16 ? 2 : 1), C2>(xs, m, make_modct<L2>(d.red[2]), DivCT<L1>(), lut, (C2)expected, mx,
                                      d.max_value, limit, S);
                 done = true;
             }
@@ -699,10 +803,10 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
         if (!done) {
             const DivRT dv{unit_magic(unit)};
             if (counter_fits32(m, w, np))
-                x = search_lower<uint32_t>(xs, m, mrt, dv, S.lut32, (uint32_t)expected, mx,
+                x = search_lower<1, uint32_t>(xs, m, mrt, dv, S.lut32, (uint32_t)expected, mx,
                                            d.max_value, limit, S);
             else
-                x = search_lower<unsigned long long>(xs, m, mrt, dv, S.lut64, expected, mx,
+                x = search_lower<1, unsigned long long>(xs, m, mrt, dv, S.lut64, expected, mx,
                                                      d.max_value, limit, S);
         }
     }
@@ -784,16 +888,18 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
         uint64_t x;
         bool done = false;
         if (d.leaf_method == 0) {  // lock-step: every lane hashes all m keys per trial
+            uint32_t bmask = 0;
+            for (uint32_t i = 0; i < m; i++) bmask |= (uint32_t)A.bb[off + i] << i;
             if constexpr (LEAF != 0) {
-                if (m == (uint32_t)LEAF) {  // full leaf: compile-time modulus
-                    x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
-                                   : leaf_plain(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
+                if (m == (uint32_t)LEAF) {  // full leaf: compile-time m and modulus
+                    x = d.rotation ? leaf_rotation<LEAF>(xs, bmask, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
+                                   : leaf_plain<LEAF>(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
                     done = true;
                 }
             }
             if (!done)
-                x = d.rotation ? leaf_rotation(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane)
-                               : leaf_plain(xs, m, make_mod(m), mx, d.max_value, limit, lane);
+                x = d.rotation ? leaf_rotation<0>(xs, bmask, m, make_mod(m), mx, d.max_value, limit, lane)
+                               : leaf_plain<0>(xs, m, make_mod(m), mx, d.max_value, limit, lane);
         } else {  // early rejection (1), with the rotation lookup table (2)
             const bool use_lut = d.leaf_method == 2 && m <= 16 && d.rot_canon;
             const uint8_t *canon = use_lut ? d.rot_canon + ((1u << m) - 4) : nullptr;

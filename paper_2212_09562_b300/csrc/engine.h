@@ -48,6 +48,15 @@ uint64_t launches_total();
 // Stage launchers (all asynchronous on `st`).
 void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint64_t *counts,
                     cudaStream_t st);
+// Two-level counting sort (nb <= 8192): number of blocks for n keys, 0 when
+// the build must use launch_fp_hist / launch_scatter instead.  blk holds
+// G * nb counters.
+uint32_t sort_blocks(uint64_t n, uint64_t nb);
+void launch_fp_hist_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint32_t G,
+                        uint64_t *counts, uint32_t *blk, cudaStream_t st);
+void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint32_t G,
+                        const uint64_t *bucket_off, uint32_t *blk, uint64_t *lo, uint8_t *bb,
+                        cudaStream_t st);
 void launch_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab, uint64_t *node_cnt,
                  uint32_t *status, uint32_t *max_m, uint64_t *size_hist, cudaStream_t st);
 // Work items of one instance ordered by decreasing bucket size; size_off is

@@ -61,6 +61,8 @@ SMALL = [(8, 100, False, 8, n) for n in (1, 2, 7, 8, 9, 100, 307, 5000)] + [
     (16, 2000, True, 8, 2500), (16, 300, True, 8, 3001), (5, 7, True, 8, 3000),
     (2, 5, True, 8, 500), (3, 40, False, 8, 800), (10, 250, True, 16, 2600),
     (20, 3, True, 8, 700), (7, 3000, True, 8, 6100), (16, 17, False, 8, 400),
+    # more than 8192 buckets: the global-atomic bucket sort instead of the two-level one
+    (8, 10, True, 8, 100_000), (5, 5, False, 16, 60_000),
 ]
 
 
