@@ -28,6 +28,13 @@ EBUCKET = -7
 
 MAX_BUCKET = 4096
 DEFAULT_MAX_VALUE = (1 << 40) - 1
+
+# leaf bijection methods (the ``rotation`` argument below takes a bool or one of these)
+PLAIN = 0
+ROTATION = 1
+SHOCKHASH = 2
+SH_SEED_BITS = 40          # a ShockHash leaf word: seed in bits 0..39, retrieval vector above
+SH_RETRIEVAL_LEVEL = 63    # salt level of the retrieval rows
 STAT_KINDS = ("leaf", "lower1", "lower2", "upper")
 
 _lock = threading.Lock()
@@ -87,6 +94,10 @@ def lib() -> ctypes.CDLL:
             L.orc_copy_out.argtypes = [p, p, p, p, p, p, p, p]
             L.orc_node_search.restype = ctypes.c_int
             L.orc_node_search.argtypes = [u32, ctypes.c_int, p, p, u32, u32, u64, p, p]
+            L.orc_shockhash_orient_prob.restype = ctypes.c_double
+            L.orc_shockhash_orient_prob.argtypes = [u32]
+            L.orc_retrieval_solvable_prob.restype = ctypes.c_double
+            L.orc_retrieval_solvable_prob.argtypes = [u32]
             L.orc_leaf_plain_early_exit.restype = u64
             L.orc_leaf_plain_early_exit.argtypes = [p, u32, p]
             _lib = L
@@ -95,6 +106,14 @@ def lib() -> ctypes.CDLL:
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def bij(rotation) -> int:
+    """Leaf method code from a bool (rotation fitting on/off) or PLAIN/ROTATION/SHOCKHASH."""
+    v = int(rotation)
+    if v not in (PLAIN, ROTATION, SHOCKHASH):
+        raise ValueError(f"unknown leaf method {rotation!r}")
+    return v
 
 
 def _key_bytes(keys: np.ndarray) -> tuple[np.ndarray, int]:
@@ -165,9 +184,17 @@ def kiely_tau(p: float) -> int:
     return int(lib().orc_kiely_tau(p))
 
 
-def tau_table(leaf: int, rotation: bool, max_m: int = MAX_BUCKET) -> np.ndarray:
+def shockhash_orient_prob(m: int) -> float:
+    return float(lib().orc_shockhash_orient_prob(m))
+
+
+def retrieval_solvable_prob(m: int) -> float:
+    return float(lib().orc_retrieval_solvable_prob(m))
+
+
+def tau_table(leaf: int, rotation, max_m: int = MAX_BUCKET) -> np.ndarray:
     out = np.zeros(max_m + 1, np.uint8)
-    lib().orc_tau_table(leaf, 1 if rotation else 0, max_m, _ptr(out))
+    lib().orc_tau_table(leaf, bij(rotation), max_m, _ptr(out))
     return out
 
 
@@ -219,18 +246,18 @@ class OracleError(RuntimeError):
         self.code = code
 
 
-def build_mphf(keys: np.ndarray, leaf: int, bucket: int, rotation: bool = True,
+def build_mphf(keys: np.ndarray, leaf: int, bucket: int, rotation=True,
                max_value: int = DEFAULT_MAX_VALUE, threads: int = 1) -> OracleMPHF:
     k, kb = _key_bytes(keys)
     h = ctypes.c_void_p()
-    rc = lib().orc_build(_ptr(k), k.shape[0], kb, leaf, bucket, 1 if rotation else 0, max_value,
+    rc = lib().orc_build(_ptr(k), k.shape[0], kb, leaf, bucket, bij(rotation), max_value,
                          threads, ctypes.byref(h))
     if rc != OK:
         raise OracleError(rc)
     return OracleMPHF(h.value, kb)
 
 
-def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation: bool, buckets: np.ndarray,
+def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation, buckets: np.ndarray,
                  max_value: int = DEFAULT_MAX_VALUE, threads: int = 1):
     """Values of the listed buckets only: (values concatenated in list order,
     node count per listed bucket, stats dict)."""
@@ -240,7 +267,7 @@ def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation: bool, bucke
     cap = MAX_BUCKET * len(buckets)  # a bucket has fewer stored nodes than keys
     vals = np.zeros(max(cap, 1), np.uint64)
     st = np.zeros(8, np.uint64)
-    rc = lib().orc_build_sample(_ptr(k), k.shape[0], kb, leaf, bucket, 1 if rotation else 0,
+    rc = lib().orc_build_sample(_ptr(k), k.shape[0], kb, leaf, bucket, bij(rotation),
                                 max_value, threads, _ptr(buckets), len(buckets), _ptr(vals),
                                 _ptr(counts), _ptr(st))
     if rc != OK:
@@ -250,14 +277,14 @@ def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation: bool, bucke
     return vals[:total].copy(), counts, stats
 
 
-def node_search(leaf: int, rotation: bool, lo: np.ndarray, hi: np.ndarray | None = None,
+def node_search(leaf: int, rotation, lo: np.ndarray, hi: np.ndarray | None = None,
                 depth: int = 0, max_value: int = DEFAULT_MAX_VALUE):
     """Search one node's value directly: returns (rc, value, trials, evals)."""
     lo = np.ascontiguousarray(lo, dtype=np.uint64)
     hi = np.zeros_like(lo) if hi is None else np.ascontiguousarray(hi, dtype=np.uint64)
     x = np.zeros(1, np.uint64)
     st = np.zeros(2, np.uint64)
-    rc = lib().orc_node_search(leaf, 1 if rotation else 0, _ptr(lo), _ptr(hi), len(lo), depth,
+    rc = lib().orc_node_search(leaf, bij(rotation), _ptr(lo), _ptr(hi), len(lo), depth,
                                max_value, _ptr(x), _ptr(st))
     return rc, int(x[0]), int(st[0]), int(st[1])
 

@@ -28,6 +28,18 @@
  *   R6  Golomb-Rice parameter per node from Kiely's rule for a geometric
  *       source; the success probability of a rotation leaf uses the bound of
  *       the Appendix A lemma.
+ *   R7  ShockHash leaves (Appendix C): under seed s a key has the two cells
+ *       (h mod 2^32) mod m and (h >> 32) mod m of h = mix64(lo + salt(0) + s).
+ *       The cells of the m keys must admit a bijection, i.e. every connected
+ *       component of the cuckoo graph has as many keys as cells.  The
+ *       canonical choice: tree edges point away from the cycle; on each cycle
+ *       the key with the smallest lo word takes its first cell.  The chosen
+ *       bit of every key is retrieved through one GF(2) equation per key,
+ *       row = mix64(lo + salt(63) + s) mod 2^m, value = parity(row & Z); Z is
+ *       the solution whose non-pivot coordinates (reduced row echelon form,
+ *       pivots at the lowest set bit) are zero.  The stored value is the
+ *       smallest s for which the graph admits a bijection and the system is
+ *       solvable, with Z in bits 40.. of the stored word.
  *
  * Parity pins: see the oracle test files (fixed points from the paper's
  * figures, closed forms, invariants, brute force on tiny inputs).  The
@@ -51,6 +63,14 @@
 #define ORC_MAX_LEAF 24u
 #define ORC_MAX_PARTS 16u
 #define ORC_GOLDEN 0x9E3779B97F4A7C15ull
+
+/* leaf bijection methods */
+#define ORC_BIJ_PLAIN 0
+#define ORC_BIJ_ROTATION 1
+#define ORC_BIJ_SHOCKHASH 2
+#define ORC_SH_SEED_BITS 40 /* ShockHash: seed in bits 0..39, retrieval vector above */
+#define ORC_SH_SEED_MASK ((1ull << ORC_SH_SEED_BITS) - 1)
+#define ORC_SH_RETRIEVAL_LEVEL 63u
 
 enum { KIND_NONE = 0, KIND_LEAF = 1, KIND_LOWER1 = 2, KIND_LOWER2 = 3, KIND_UPPER = 4 };
 enum { ST_LEAF = 0, ST_LOWER1 = 1, ST_LOWER2 = 2, ST_UPPER = 3, ST_N = 4 };
@@ -297,6 +317,201 @@ static int leaf_rotation(const uint64_t *lo, const uint64_t *hi, uint32_t m, uin
 }
 
 /* ------------------------------------------------------------------------ */
+/* R7: ShockHash leaves (Appendix C).  A trial is a pair of hash functions; */
+/* the m keys are the edges of a multigraph on the m cells (a loop when     */
+/* both cells agree).  A bijection picking one cell per key exists iff no   */
+/* component has more keys than cells (with m keys on m cells: iff every    */
+/* component has exactly one cycle).                                        */
+/* ------------------------------------------------------------------------ */
+static double binom(uint32_t n, uint32_t k);
+
+static void sh_cells(uint64_t lo, uint64_t s, uint32_t m, uint32_t *c0, uint32_t *c1) {
+    uint64_t h = orc_mix64(lo + orc_salt(0) + s);
+    *c0 = (uint32_t)(h & 0xFFFFFFFFu) % m;
+    *c1 = (uint32_t)(h >> 32) % m;
+}
+
+/* Union-find over the cells; orientable iff edges == cells in every component. */
+static int sh_orientable(const uint32_t *c0, const uint32_t *c1, uint32_t m) {
+    uint32_t comp[ORC_MAX_LEAF], cells[ORC_MAX_LEAF], edges[ORC_MAX_LEAF];
+    for (uint32_t v = 0; v < m; v++) {
+        comp[v] = v;
+        cells[v] = 1;
+        edges[v] = 0;
+    }
+    for (uint32_t i = 0; i < m; i++) {
+        uint32_t a = comp[c0[i]], b = comp[c1[i]];
+        if (a != b) { /* merge component b into a */
+            for (uint32_t v = 0; v < m; v++)
+                if (comp[v] == b) comp[v] = a;
+            cells[a] += cells[b];
+            edges[a] += edges[b];
+        }
+        edges[a] += 1;
+    }
+    for (uint32_t v = 0; v < m; v++)
+        if (comp[v] == v && edges[v] != cells[v]) return 0;
+    return 1;
+}
+
+/* The canonical bijection of an orientable trial: beta[i] = 0 if key i takes
+ * cell c0[i], 1 if c1[i].  First every cell of degree one takes its only
+ * remaining key (the trees hanging off the cycles), then each remaining
+ * cycle is walked from its key with the smallest lo word, which takes its
+ * first cell. */
+static void sh_orientation(const uint64_t *lo, const uint32_t *c0, const uint32_t *c1, uint32_t m,
+                           uint8_t *beta) {
+    uint32_t deg[ORC_MAX_LEAF];
+    uint8_t alive[ORC_MAX_LEAF];
+    memset(deg, 0, sizeof(deg));
+    for (uint32_t i = 0; i < m; i++) {
+        deg[c0[i]]++;
+        deg[c1[i]]++;
+        alive[i] = 1;
+        beta[i] = 0;
+    }
+    for (;;) { /* peel cells of degree one */
+        uint32_t c = m;
+        for (uint32_t v = 0; v < m && c == m; v++)
+            if (deg[v] == 1) c = v;
+        if (c == m) break;
+        uint32_t e = m;
+        for (uint32_t i = 0; i < m && e == m; i++)
+            if (alive[i] && (c0[i] == c || c1[i] == c)) e = i;
+        beta[e] = c0[e] == c ? 0 : 1;
+        alive[e] = 0;
+        uint32_t other = c0[e] == c ? c1[e] : c0[e];
+        deg[c] = 0;
+        deg[other]--;
+    }
+    for (;;) { /* the cycles */
+        uint32_t e0 = m;
+        for (uint32_t i = 0; i < m; i++)
+            if (alive[i] && (e0 == m || lo[i] < lo[e0])) e0 = i;
+        if (e0 == m) break;
+        beta[e0] = 0;
+        alive[e0] = 0;
+        uint32_t start = c0[e0], cur = c1[e0];
+        while (cur != start) {
+            uint32_t e = m;
+            for (uint32_t i = 0; i < m && e == m; i++)
+                if (alive[i] && (c0[i] == cur || c1[i] == cur)) e = i;
+            beta[e] = c0[e] == cur ? 0 : 1;
+            alive[e] = 0;
+            cur = c0[e] == cur ? c1[e] : c0[e];
+        }
+    }
+}
+
+/* Retrieval of one bit per key: solve row_i . Z = rhs_i over GF(2) by
+ * Gauss-Jordan elimination, columns in increasing order, pivot row of a
+ * column = the first remaining row with that bit.  Returns 1 and the
+ * solution with zero non-pivot coordinates, or 0 if inconsistent. */
+static int sh_solve(const uint32_t *row_in, const uint8_t *rhs_in, uint32_t m, uint32_t *z) {
+    uint32_t row[ORC_MAX_LEAF];
+    uint8_t rhs[ORC_MAX_LEAF], piv[ORC_MAX_LEAF];
+    int32_t col_row[32];
+    for (uint32_t i = 0; i < m; i++) {
+        row[i] = row_in[i];
+        rhs[i] = rhs_in[i];
+        piv[i] = 0;
+    }
+    for (uint32_t j = 0; j < m; j++) {
+        col_row[j] = -1;
+        uint32_t p = m;
+        for (uint32_t i = 0; i < m && p == m; i++)
+            if (!piv[i] && ((row[i] >> j) & 1)) p = i;
+        if (p == m) continue;
+        piv[p] = 1;
+        col_row[j] = (int32_t)p;
+        for (uint32_t i = 0; i < m; i++)
+            if (i != p && ((row[i] >> j) & 1)) {
+                row[i] ^= row[p];
+                rhs[i] ^= rhs[p];
+            }
+    }
+    for (uint32_t i = 0; i < m; i++)
+        if (!piv[i] && rhs[i]) return 0; /* a zero row with value one */
+    uint32_t out = 0;
+    for (uint32_t j = 0; j < m; j++)
+        if (col_row[j] >= 0 && rhs[col_row[j]]) out |= 1u << j;
+    *z = out;
+    return 1;
+}
+
+static uint32_t sh_row(uint64_t lo, uint64_t s, uint32_t m) {
+    uint64_t h = orc_mix64(lo + orc_salt(ORC_SH_RETRIEVAL_LEVEL) + s);
+    return (uint32_t)(h & ((1ull << m) - 1));
+}
+
+static int leaf_shockhash(const uint64_t *lo, uint32_t m, uint64_t max_value, uint64_t *out,
+                          orc_stats *st) {
+    uint32_t c0[ORC_MAX_LEAF], c1[ORC_MAX_LEAF], rows[ORC_MAX_LEAF];
+    uint8_t beta[ORC_MAX_LEAF];
+    if (max_value > ORC_SH_SEED_MASK) max_value = ORC_SH_SEED_MASK;
+    for (uint64_t s = 0;; s++) {
+        for (uint32_t i = 0; i < m; i++) sh_cells(lo[i], s, m, &c0[i], &c1[i]);
+        st->trials[ST_LEAF]++;
+        st->evals[ST_LEAF] += m;
+        if (sh_orientable(c0, c1, m)) {
+            sh_orientation(lo, c0, c1, m, beta);
+            for (uint32_t i = 0; i < m; i++) rows[i] = sh_row(lo[i], s, m);
+            uint32_t z;
+            if (sh_solve(rows, beta, m, &z)) {
+                *out = s | ((uint64_t)z << ORC_SH_SEED_BITS);
+                return ORC_OK;
+            }
+        }
+        if (s == max_value) return ORC_ESEARCH_LIMIT;
+    }
+}
+
+/* Probability that m keys with two uniform cells each (out of m) admit a
+ * bijection.  Counting labelled edge lists with ordered cell pairs: the
+ * pairs (list, valid choice vector) number m! 2^m m^m (pick the bijection,
+ * the bits, the free cell), and a list whose components are all unicyclic
+ * has 2 choices per component.  With W(k) = k! 2^k k^k, the connected
+ * unicyclic lists U(k) follow from W(k) = sum_j C(k-1,j-1) C(k,j) 2U(j)
+ * W(k-j) (the component of cell 0 has j cells and j keys), and the
+ * orientable lists O(k) = sum_j C(k-1,j-1) C(k,j) U(j) O(k-j). */
+double orc_shockhash_orient_prob(uint32_t m) {
+    double W[ORC_MAX_LEAF + 1], U[ORC_MAX_LEAF + 1], O[ORC_MAX_LEAF + 1];
+    if (m == 0 || m > ORC_MAX_LEAF) return 0.0;
+    W[0] = 1.0;
+    O[0] = 1.0;
+    for (uint32_t k = 1; k <= m; k++) {
+        double w = 1.0;
+        for (uint32_t i = 1; i <= k; i++) w *= (double)i * 2.0 * (double)k;
+        W[k] = w;
+        double rest = 0.0;
+        for (uint32_t j = 1; j < k; j++) rest += binom(k - 1, j - 1) * binom(k, j) * 2.0 * U[j] * W[k - j];
+        U[k] = (W[k] - rest) / 2.0;
+        double o = 0.0;
+        for (uint32_t j = 1; j <= k; j++) o += binom(k - 1, j - 1) * binom(k, j) * U[j] * O[k - j];
+        O[k] = o;
+    }
+    return O[m] / pow((double)m, 2.0 * (double)m);
+}
+
+/* Probability that m uniform random GF(2) rows of m bits give a solvable
+ * system for a fixed nonzero right-hand side: sum over the rank r of
+ * P(rank r) * (2^r - 1)/(2^m - 1), the column space being a uniform
+ * r-dimensional subspace; P(rank r) = 2^-(m-r)^2 prod_{i<r}
+ * (1 - 2^(i-m))^2 / (1 - 2^(i-r)). */
+double orc_retrieval_solvable_prob(uint32_t m) {
+    double total = 0.0;
+    for (uint32_t r = 0; r <= m; r++) {
+        double p = ldexp(1.0, -(int)((m - r) * (m - r)));
+        for (uint32_t i = 0; i < r; i++) {
+            double a = 1.0 - ldexp(1.0, (int)i - (int)m);
+            p *= a * a / (1.0 - ldexp(1.0, (int)i - (int)r));
+        }
+        total += p * (ldexp(1.0, (int)r) - 1.0) / (ldexp(1.0, (int)m) - 1.0);
+    }
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
 /* R6: Golomb-Rice parameter per node (Section 2.2 "Representation": the    */
 /* optimal parameter depends on the layer and is precomputed).              */
 /* ------------------------------------------------------------------------ */
@@ -380,18 +595,32 @@ uint32_t orc_kiely_tau(double p) {
     return t < 0.0 ? 0u : (uint32_t)t;
 }
 
-/* Success probability per stored unit of the node of m keys. */
-static double unit_success(const orc_shape *sh, int rotation, uint32_t m) {
-    if (kind_of(sh, m) == KIND_LEAF)
-        return rotation ? orc_rotation_success_bound(m) / (double)m : orc_plain_success(m);
+/* Success probability per stored unit of the node of m keys.  A ShockHash
+ * trial succeeds when the graph admits a bijection and the retrieval system
+ * of its chosen bits is solvable (taken as independent events). */
+static double unit_success(const orc_shape *sh, int bij, uint32_t m) {
+    if (kind_of(sh, m) == KIND_LEAF) {
+        if (bij == ORC_BIJ_ROTATION) return orc_rotation_success_bound(m) / (double)m;
+        if (bij == ORC_BIJ_SHOCKHASH)
+            return orc_shockhash_orient_prob(m) * orc_retrieval_solvable_prob(m);
+        return orc_plain_success(m);
+    }
     return split_success(sh, m);
 }
 
 /* tau[m] for every node size m in [0, max_m]; m < 2 gives 0. */
-void orc_tau_table(uint32_t leaf, int rotation, uint32_t max_m, uint8_t *tau) {
+void orc_tau_table(uint32_t leaf, int bij, uint32_t max_m, uint8_t *tau) {
     orc_shape sh = shape_of(leaf);
     for (uint32_t m = 0; m <= max_m; m++)
-        tau[m] = m < 2 ? 0 : (uint8_t)orc_kiely_tau(unit_success(&sh, rotation, m));
+        tau[m] = m < 2 ? 0 : (uint8_t)orc_kiely_tau(unit_success(&sh, bij, m));
+}
+
+/* Fixed-part width of a node: tau bits of the value, plus the m retrieval
+ * bits of a ShockHash leaf. */
+static uint32_t fixed_width(const orc_shape *sh, int bij, const uint8_t *tau, uint32_t m) {
+    uint32_t w = tau[m];
+    if (bij == ORC_BIJ_SHOCKHASH && kind_of(sh, m) == KIND_LEAF) w += m;
+    return w;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -459,7 +688,7 @@ found:;
 /* ------------------------------------------------------------------------ */
 typedef struct orc_mphf {
     uint64_t n, nb;
-    uint32_t leaf, bucket_size, rotation, key_bytes;
+    uint32_t leaf, bucket_size, bij, key_bytes; /* bij: ORC_BIJ_* leaf method */
     uint64_t *cum_keys; /* nb+1: keys in buckets before i              */
     uint64_t *node_off; /* nb+1: first stored node of bucket i          */
     uint64_t *values;   /* node_off[nb] values, preorder in each bucket */
@@ -474,7 +703,7 @@ typedef struct orc_mphf {
     orc_stats stats;
 } orc_mphf;
 
-static void fill_subtree_tables(const orc_shape *sh, const uint8_t *tau, uint32_t max_m,
+static void fill_subtree_tables(const orc_shape *sh, int bij, const uint8_t *tau, uint32_t max_m,
                                 uint64_t *nodes_tab, uint64_t *fixed_tab) {
     for (uint32_t m = 0; m <= max_m; m++) {
         if (m <= 1) {
@@ -484,7 +713,7 @@ static void fill_subtree_tables(const orc_shape *sh, const uint8_t *tau, uint32_
         }
         uint32_t parts[ORC_MAX_PARTS];
         uint32_t np = parts_of(sh, m, parts);
-        uint64_t c = 1, f = tau[m];
+        uint64_t c = 1, f = fixed_width(sh, bij, tau, m);
         for (uint32_t i = 0; i < np; i++) {
             c += nodes_tab[parts[i]];
             f += fixed_tab[parts[i]];
@@ -497,7 +726,7 @@ static void fill_subtree_tables(const orc_shape *sh, const uint8_t *tau, uint32_
 /* Per-bucket work: keys of one bucket, its search results in preorder. */
 typedef struct {
     const orc_shape *sh;
-    int rotation;
+    int bij;
     uint64_t max_value;
     uint64_t *values; /* where this bucket's nodes go */
     uint64_t count;   /* nodes written so far          */
@@ -515,8 +744,12 @@ static int build_node(bucket_ctx *cx, uint64_t *lo, uint64_t *hi, uint64_t *tlo,
     uint64_t x;
     int rc;
     if (kind == KIND_LEAF) {
-        rc = cx->rotation ? leaf_rotation(lo, hi, m, cx->max_value, &x, cx->st)
-                          : leaf_plain(lo, m, cx->max_value, &x, cx->st);
+        if (cx->bij == ORC_BIJ_ROTATION)
+            rc = leaf_rotation(lo, hi, m, cx->max_value, &x, cx->st);
+        else if (cx->bij == ORC_BIJ_SHOCKHASH)
+            rc = leaf_shockhash(lo, m, cx->max_value, &x, cx->st);
+        else
+            rc = leaf_plain(lo, m, cx->max_value, &x, cx->st);
         if (rc) return rc;
         cx->values[cx->count++] = x;
         return ORC_OK;
@@ -611,7 +844,7 @@ static void free_grouped(grouped *g) {
 typedef struct {
     const grouped *g;
     const orc_shape *sh;
-    int rotation;
+    int bij;
     uint64_t max_value;
     const uint64_t *bucket_list; /* buckets to build, in output order */
     const uint64_t *out_off;     /* first output node per list entry  */
@@ -647,7 +880,7 @@ static void *worker_run(void *arg) {
             }
             continue;
         }
-        bucket_ctx cx = {w->sh, w->rotation, w->max_value, w->values + w->out_off[j], 0, &w->st};
+        bucket_ctx cx = {w->sh, w->bij, w->max_value, w->values + w->out_off[j], 0, &w->st};
         int rc = build_node(&cx, lo, hi, tlo, thi, m, 0);
         if (rc) {
             w->rc = rc;
@@ -663,7 +896,7 @@ done:
 }
 
 /* Runs the duplicate check over all listed buckets, then the searches. */
-static int run_buckets(const grouped *g, const orc_shape *sh, int rotation, uint64_t max_value,
+static int run_buckets(const grouped *g, const orc_shape *sh, int bij, uint64_t max_value,
                        const uint64_t *list, const uint64_t *out_off, uint64_t count,
                        uint64_t *values, int threads, orc_stats *st) {
     if (threads < 1) threads = 1;
@@ -678,7 +911,7 @@ static int run_buckets(const grouped *g, const orc_shape *sh, int rotation, uint
     for (int phase = 0; phase < 2 && rc == ORC_OK; phase++) {
         for (int t = 0; t < threads; t++) {
             worker *w = &ws[t];
-            w->g = g; w->sh = sh; w->rotation = rotation; w->max_value = max_value;
+            w->g = g; w->sh = sh; w->bij = bij; w->max_value = max_value;
             w->bucket_list = list; w->out_off = out_off; w->values = values;
             w->first = count * (uint64_t)t / (uint64_t)threads;
             w->last = count * (uint64_t)(t + 1) / (uint64_t)threads;
@@ -707,7 +940,9 @@ static int run_buckets(const grouped *g, const orc_shape *sh, int rotation, uint
     return rc;
 }
 
-static int check_params(uint64_t n, uint32_t key_bytes, uint32_t leaf, uint32_t bucket_size) {
+static int check_params(uint64_t n, uint32_t key_bytes, uint32_t leaf, uint32_t bucket_size,
+                        int bij) {
+    if (bij < ORC_BIJ_PLAIN || bij > ORC_BIJ_SHOCKHASH) return ORC_EINVAL;
     if (key_bytes != 8 && key_bytes != 16) return ORC_EINVAL;
     if (leaf < 2 || leaf > ORC_MAX_LEAF) return ORC_EINVAL;
     if (bucket_size < 1 || bucket_size > 3000) return ORC_EINVAL;
@@ -724,13 +959,23 @@ void orc_free(orc_mphf *h) {
 
 /* Golomb-Rice writer (Section 2.1; Section 2.2 "Representation": per tree,
  * all fixed parts in preorder, then all unary parts in preorder). */
-static uint64_t bucket_bits(const orc_mphf *h, uint32_t m, const uint64_t *vals,
+static int is_shock_leaf(const orc_mphf *h, const orc_shape *sh, uint32_t m) {
+    return h->bij == ORC_BIJ_SHOCKHASH && kind_of(sh, m) == KIND_LEAF;
+}
+
+/* The Golomb-Rice coded number of a stored word: the seed of a ShockHash
+ * leaf (its retrieval vector goes to the fixed part verbatim), else the word. */
+static uint64_t coded_value(const orc_mphf *h, const orc_shape *sh, uint32_t m, uint64_t v) {
+    return is_shock_leaf(h, sh, m) ? (v & ORC_SH_SEED_MASK) : v;
+}
+
+static uint64_t bucket_bits(const orc_mphf *h, const orc_shape *sh, const uint64_t *vals,
                             const uint32_t *sizes, uint64_t count) {
-    (void)m;
     uint64_t bits = 0;
     for (uint64_t j = 0; j < count; j++) {
         uint32_t t = h->tau[sizes[j]];
-        bits += t + 1 + (vals[j] >> t);
+        bits += fixed_width(sh, (int)h->bij, h->tau, sizes[j]) + 1 +
+                (coded_value(h, sh, sizes[j], vals[j]) >> t);
     }
     return bits;
 }
@@ -747,10 +992,10 @@ static void preorder_sizes(const orc_shape *sh, uint32_t m, uint32_t *out, uint6
 
 /* Full build.  Returns ORC_OK and a new function in *out, or an error. */
 int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf,
-              uint32_t bucket_size, int rotation, uint64_t max_value, int threads,
+              uint32_t bucket_size, int bij, uint64_t max_value, int threads,
               orc_mphf **out) {
     *out = NULL;
-    int rc = check_params(n, key_bytes, leaf, bucket_size);
+    int rc = check_params(n, key_bytes, leaf, bucket_size, bij);
     if (rc) return rc;
     orc_shape sh = shape_of(leaf);
     uint64_t nb = (n + bucket_size - 1) / bucket_size;
@@ -760,7 +1005,7 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
     orc_mphf *h = calloc(1, sizeof(orc_mphf));
     if (!h) { free_grouped(&g); return ORC_ENOMEM; }
     h->n = n; h->nb = nb; h->leaf = leaf; h->bucket_size = bucket_size;
-    h->rotation = rotation ? 1 : 0; h->key_bytes = key_bytes;
+    h->bij = (uint32_t)bij; h->key_bytes = key_bytes;
     h->tau = malloc(ORC_MAX_BUCKET + 1);
     h->nodes_tab = malloc((ORC_MAX_BUCKET + 1) * sizeof(uint64_t));
     h->fixed_tab = malloc((ORC_MAX_BUCKET + 1) * sizeof(uint64_t));
@@ -773,8 +1018,8 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
         rc = ORC_ENOMEM;
         goto fail;
     }
-    orc_tau_table(leaf, h->rotation, ORC_MAX_BUCKET, h->tau);
-    fill_subtree_tables(&sh, h->tau, ORC_MAX_BUCKET, h->nodes_tab, h->fixed_tab);
+    orc_tau_table(leaf, bij, ORC_MAX_BUCKET, h->tau);
+    fill_subtree_tables(&sh, bij, h->tau, ORC_MAX_BUCKET, h->nodes_tab, h->fixed_tab);
     memcpy(h->cum_keys, g.cum, (nb + 1) * sizeof(uint64_t));
     h->node_off[0] = 0;
     for (uint64_t b = 0; b < nb; b++) {
@@ -785,7 +1030,7 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
     }
     h->values = calloc(h->node_off[nb] ? h->node_off[nb] : 1, sizeof(uint64_t));
     if (!h->values) { rc = ORC_ENOMEM; goto fail; }
-    rc = run_buckets(&g, &sh, h->rotation, max_value, list, h->node_off, nb, h->values, threads,
+    rc = run_buckets(&g, &sh, bij, max_value, list, h->node_off, nb, h->values, threads,
                      &h->stats);
     if (rc) goto fail;
 
@@ -798,7 +1043,7 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
             uint32_t m = (uint32_t)(g.cum[b + 1] - g.cum[b]);
             uint64_t cnt = 0;
             preorder_sizes(&sh, m, sizes, &cnt);
-            h->bit_pos[b + 1] = h->bit_pos[b] + bucket_bits(h, m, h->values + h->node_off[b], sizes, cnt);
+            h->bit_pos[b + 1] = h->bit_pos[b] + bucket_bits(h, &sh, h->values + h->node_off[b], sizes, cnt);
         }
         h->gr_bits = h->bit_pos[nb];
         h->gr_words = (h->gr_bits + 63) / 64;
@@ -812,12 +1057,19 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
             uint64_t pos = h->bit_pos[b];
             for (uint64_t j = 0; j < cnt; j++) { /* fixed parts */
                 uint32_t t = h->tau[sizes[j]];
+                uint64_t x = coded_value(h, &sh, sizes[j], vals[j]);
                 for (uint32_t i = 0; i < t; i++)
-                    if ((vals[j] >> i) & 1) set_bit(h->gr, pos + i);
+                    if ((x >> i) & 1) set_bit(h->gr, pos + i);
                 pos += t;
+                if (is_shock_leaf(h, &sh, sizes[j])) { /* the retrieval vector */
+                    uint64_t z = vals[j] >> ORC_SH_SEED_BITS;
+                    for (uint32_t i = 0; i < sizes[j]; i++)
+                        if ((z >> i) & 1) set_bit(h->gr, pos + i);
+                    pos += sizes[j];
+                }
             }
             for (uint64_t j = 0; j < cnt; j++) { /* unary parts */
-                pos += vals[j] >> h->tau[sizes[j]];
+                pos += coded_value(h, &sh, sizes[j], vals[j]) >> h->tau[sizes[j]];
                 set_bit(h->gr, pos);
                 pos++;
             }
@@ -854,10 +1106,10 @@ fail:
  * values, bucket after bucket in list order, each in preorder.  Used to
  * check large builds on a sample of buckets. */
 int orc_build_sample(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf,
-                     uint32_t bucket_size, int rotation, uint64_t max_value, int threads,
+                     uint32_t bucket_size, int bij, uint64_t max_value, int threads,
                      const uint64_t *buckets, uint64_t count, uint64_t *values_out,
                      uint64_t *node_counts, uint64_t *stats_out) {
-    int rc = check_params(n, key_bytes, leaf, bucket_size);
+    int rc = check_params(n, key_bytes, leaf, bucket_size, bij);
     if (rc) return rc;
     orc_shape sh = shape_of(leaf);
     uint64_t nb = (n + bucket_size - 1) / bucket_size;
@@ -876,8 +1128,7 @@ int orc_build_sample(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32
     }
     orc_stats st;
     memset(&st, 0, sizeof(st));
-    rc = run_buckets(&g, &sh, rotation ? 1 : 0, max_value, buckets, off, count, values_out,
-                     threads, &st);
+    rc = run_buckets(&g, &sh, bij, max_value, buckets, off, count, values_out, threads, &st);
     if (stats_out)
         for (int k = 0; k < ST_N; k++) {
             stats_out[2 * k] = st.trials[k];
@@ -942,7 +1193,18 @@ static uint64_t query_one(const orc_mphf *h, const orc_shape *sh, uint64_t hi, u
     }
     if (m <= 1) return cum + rank;
     uint64_t x = node_value(h, fixed_pos, h->tau[m], unary_start, idx);
-    if (!h->rotation) return cum + rank + orc_mix64(lo + orc_salt(0) + x) % m;
+    if (h->bij == ORC_BIJ_PLAIN) return cum + rank + orc_mix64(lo + orc_salt(0) + x) % m;
+    if (h->bij == ORC_BIJ_SHOCKHASH) {
+        /* the retrieval vector follows the seed's tau bits in the fixed part;
+         * the key's bit selects which of its two cells it occupies */
+        uint64_t z = 0;
+        for (uint32_t i = 0; i < m; i++)
+            z |= (uint64_t)get_bit(h->gr, fixed_pos + h->tau[m] + i) << i;
+        uint32_t c0, c1;
+        sh_cells(lo, x, m, &c0, &c1);
+        uint32_t bit = (uint32_t)__builtin_popcountll(sh_row(lo, x, m) & z) & 1;
+        return cum + rank + (bit ? c1 : c0);
+    }
     uint64_t r = x % m;
     uint64_t pos = orc_mix64(lo + orc_salt(0) + (x - r)) % m;
     if (hi & 1) pos = (pos + r) % m;
@@ -991,7 +1253,7 @@ void orc_copy_out(const orc_mphf *h, uint64_t *cum_keys, uint64_t *node_off, uin
 /* Single-node searches, for brute-force checks and per-node statistics.
  * kind: the node's own keys, its depth in the bucket tree (salt level of
  * fanout-2 nodes), and the values found / trials / hash evaluations. */
-int orc_node_search(uint32_t leaf, int rotation, const uint64_t *lo, const uint64_t *hi,
+int orc_node_search(uint32_t leaf, int bij, const uint64_t *lo, const uint64_t *hi,
                     uint32_t m, uint32_t depth, uint64_t max_value, uint64_t *x, uint64_t *stats) {
     orc_shape sh = shape_of(leaf);
     orc_stats st;
@@ -1000,8 +1262,9 @@ int orc_node_search(uint32_t leaf, int rotation, const uint64_t *lo, const uint6
     int kind = kind_of(&sh, m);
     if (kind == KIND_NONE) return ORC_EINVAL;
     if (kind == KIND_LEAF)
-        rc = rotation ? leaf_rotation(lo, hi, m, max_value, x, &st)
-                      : leaf_plain(lo, m, max_value, x, &st);
+        rc = bij == ORC_BIJ_ROTATION    ? leaf_rotation(lo, hi, m, max_value, x, &st)
+           : bij == ORC_BIJ_SHOCKHASH ? leaf_shockhash(lo, m, max_value, x, &st)
+                                      : leaf_plain(lo, m, max_value, x, &st);
     else
         rc = split_search(&sh, lo, m, depth, max_value, x, &st);
     if (stats) {
