@@ -42,6 +42,7 @@ OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # ncu capture of k_search on 1,200,000 keys of rot_l16: 11,084,032 B.  The
 # traffic of a launch grows with its key count.
 SEARCH_DRAM_BYTES_PER_KEY = 11_084_032 / 1_200_000
+LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 SMS, SMSP_PER_SM, LANES, SM_MAX_MHZ = 148, 4, 32, 2032.0
 PEAK_INT_OPS = SMS * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6  # issue-slot bound, lane-ops/s
 
@@ -259,7 +260,8 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
            "data": "synthetic", "impl": "reference",
            "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "bucket": w.bucket,
-                      "rotation": w.rotation, "key_bytes": w.key_bytes, "sample": r["sample"]},
+                      "rotation": int(w.rotation) == 1, "leaves": LEAF_NAMES[int(w.rotation)],
+                      "key_bytes": w.key_bytes, "sample": r["sample"]},
            "cpu_baseline": {"value": v, "unit": "keys/s", "cores": r["cores"], "kind": "oracle",
                             "sample": r["sample"]},
            "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -399,7 +401,8 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
            "data": "synthetic",
            "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "bucket": w.bucket,
-                      "rotation": w.rotation, "key_bytes": w.key_bytes,
+                      "rotation": int(w.rotation) == 1, "leaves": LEAF_NAMES[int(w.rotation)],
+                      "key_bytes": w.key_bytes,
                       "l2": "flushed between steps (256 MB write)",
                       "parallelism": f"{world} independent builds (one per GPU)"},
            "trials_per_s": world * trials / (total_ms / 1000.0),

@@ -2,7 +2,7 @@
  * mphf.h -- C ABI of the B300 RecSplit construction library (libmphf.so).
  *
  * Builds a RecSplit minimal perfect hash function (MPHF) with rotation
- * fitting on one CUDA device, after Bez, Kurpicz, Lehmann and Sanders,
+ * fitting (or plain brute-force or ShockHash leaves) on one CUDA device, after Bez, Kurpicz, Lehmann and Sanders,
  * "High Performance Construction of RecSplit Based Minimal Perfect Hash
  * Functions" (arXiv 2212.09562).  The problem (Section 1): given a set S of
  * n distinct keys, build h with h bijective from S onto [0, n); outside S the
@@ -64,20 +64,35 @@ typedef struct {
  *   leaf_size        l, 2..24 (Section 2.2: leaves of l keys).
  *   bucket_size      b, 1..3000; nb = ceil(n / b) buckets.
  *   key_bytes        8 or 16.
- *   rotation_fitting 1: leaves use rotation fitting (Section 4); 0: plain
- *                    brute force (Section 2.2, "Bijections").
+ *   leaf_bijection   how a leaf's bijection is found (the stored values
+ *                    differ between the three):
+ *                    MPHF_BIJECTION_PLAIN     brute force over seeds (Section
+ *                                             2.2, "Bijections");
+ *                    MPHF_BIJECTION_ROTATION  rotation fitting (Section 4);
+ *                    MPHF_BIJECTION_SHOCKHASH ShockHash (Appendix C): a seed
+ *                                             whose two cells per key admit a
+ *                                             bijection, one retrieved bit per
+ *                                             key choosing the cell.
  *   max_value        largest value any node may store; a node that needs
  *                    more fails the build with MPHF_ESEARCH_LIMIT.
  *   threads_per_block, blocks_per_sm
  *                    launch shape of the search kernel; 0 = the tuned or
  *                    default choice.
- *   leaf_method      how leaves are searched (same result every time):
+ *   leaf_method      how plain and rotation leaves are searched (same result
+ *                    every time; ShockHash leaves have one search):
  *                    MPHF_LEAF_LOCKSTEP  every trial hashes all m keys
  *                                        (default, the fastest measured);
  *                    MPHF_LEAF_EARLY     a trial stops at its first collision;
  *                    MPHF_LEAF_TABLE     as EARLY, the rotation from a table of
  *                                        canonical rotations (leaves of <= 16
  *                                        keys; Section 4, "Lookup Tables"). */
+#define MPHF_BIJECTION_PLAIN 0u
+#define MPHF_BIJECTION_ROTATION 1u
+#define MPHF_BIJECTION_SHOCKHASH 2u
+/* A ShockHash leaf of m keys stores its seed in bits 0..39 of the value and
+ * its m-bit retrieval vector Z in bits 40..: key x takes its second cell iff
+ * parity(row(x) & Z) = 1.  Its seed is capped at 2^40 - 1 whatever max_value. */
+#define MPHF_SH_SEED_BITS 40u
 #define MPHF_LEAF_LOCKSTEP 0u
 #define MPHF_LEAF_EARLY 1u
 #define MPHF_LEAF_TABLE 2u
@@ -85,7 +100,7 @@ typedef struct {
     uint32_t leaf_size;
     uint32_t bucket_size;
     uint32_t key_bytes;
-    uint32_t rotation_fitting;
+    uint32_t leaf_bijection;
     uint64_t max_value;
     const mphf_allocator *allocator;
     uint32_t threads_per_block;
@@ -97,7 +112,7 @@ typedef struct {
 /* Sizes and parameters of a built function. */
 typedef struct {
     uint64_t n, nb;            /* keys, buckets                                    */
-    uint32_t leaf_size, bucket_size, key_bytes, rotation_fitting;
+    uint32_t leaf_size, bucket_size, key_bytes, leaf_bijection;
     uint64_t n_nodes;          /* stored values (nodes with >= 2 keys)              */
     uint64_t gr_bits;          /* Golomb-Rice bit length                           */
     uint64_t gr_words;         /* 64-bit words holding them                        */
@@ -142,7 +157,7 @@ int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *par
                     void *stream, mphf_t **out);
 
 /* Evaluates h on n keys (Section 2.2, "Query"; Section 4 for the rotation
- * of the keys in B).  d_out[i] = h(key i) in [0, n_built) for keys of the
+ * of the keys in B; Appendix C for the retrieved cell of a ShockHash leaf).  d_out[i] = h(key i) in [0, n_built) for keys of the
  * built set.  Asynchronous on the stream. */
 int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out, void *stream);
 
@@ -171,7 +186,8 @@ int mphf_get_info(const mphf_t *h, mphf_info *info);
 /* Device arrays of a built function, owned by h:
  *   d_values   n_nodes stored values; bucket i's nodes in preorder at
  *              [d_node_off[i], d_node_off[i+1]).  A rotation leaf of m keys
- *              stores k*m + r (seed k*m, rotation r).
+ *              stores k*m + r (seed k*m, rotation r); a ShockHash leaf its
+ *              seed and retrieval vector (MPHF_SH_SEED_BITS).
  *   d_node_off nb + 1 offsets.
  *   d_cum_keys nb + 1 bucket prefix sums of key counts.
  *   d_bit_pos  nb + 1 start bits of each bucket's Golomb-Rice code. */
@@ -189,7 +205,7 @@ int mphf_get_stats(const mphf_t *h, mphf_stats *stats);
 /* Golomb-Rice parameter per node size m in [0, max_m] as the library uses it
  * (Section 2.2, "Representation": one parameter per tree layer, precomputed).
  * Writes max_m + 1 bytes to host memory. */
-int mphf_tau_table(uint32_t leaf_size, uint32_t rotation_fitting, uint32_t max_m, uint8_t *h_out);
+int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t max_m, uint8_t *h_out);
 
 /* Copies the function to host memory: a header then the Golomb-Rice and
  * Elias-Fano words.  With h_buf NULL, *len receives the size needed. */
@@ -214,7 +230,7 @@ typedef struct {
     uint32_t leaf_size;
     uint32_t bucket_size;
     uint32_t key_bytes;
-    uint32_t rotation_fitting;
+    uint32_t leaf_bijection;  /* MPHF_BIJECTION_* */
     uint64_t max_value;       /* 0 = MPHF_DEFAULT_MAX_VALUE */
 } mphf_build_desc;
 

@@ -43,8 +43,8 @@ def _device_name() -> str:
     return torch.cuda.get_device_name(torch.cuda.current_device())
 
 
-def _key(leaf: int, rotation: bool) -> str:
-    return f"{_device_name()}|l={leaf}|rot={int(bool(rotation))}"
+def _key(leaf: int, rotation) -> str:
+    return f"{_device_name()}|l={leaf}|rot={int(rotation)}"
 
 
 def tuned(leaf: int, rotation: bool = True) -> tuple[int, int]:

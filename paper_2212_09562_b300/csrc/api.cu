@@ -39,17 +39,17 @@ struct DevTables {
 };
 
 // Per-device copies of the per-size tables; live until the process exits.
-int device_tables(int dev, uint32_t leaf, uint32_t rotation, DevTables *out) {
+int device_tables(int dev, uint32_t leaf, uint32_t bij, DevTables *out) {
     static std::mutex mu;
     static std::map<uint64_t, DevTables> cache;
     std::lock_guard<std::mutex> g(mu);
-    uint64_t key = ((uint64_t)dev << 32) | (leaf << 1) | (rotation ? 1 : 0);
+    uint64_t key = ((uint64_t)dev << 32) | (leaf << 2) | bij;
     auto it = cache.find(key);
     if (it != cache.end()) {
         *out = it->second;
         return MPHF_OK;
     }
-    const SizeTables &t = size_tables(leaf, rotation);
+    const SizeTables &t = size_tables(leaf, bij);
     DevTables d;
     if (cudaMalloc(&d.tau, sizeof(t.tau)) != cudaSuccess) return MPHF_ENOMEM;
     if (cudaMalloc(&d.nodes, sizeof(t.nodes)) != cudaSuccess) return MPHF_ENOMEM;
@@ -186,7 +186,7 @@ void mphf_default_params(mphf_build_params *p) {
     p->leaf_size = 16;
     p->bucket_size = 2000;
     p->key_bytes = 8;
-    p->rotation_fitting = 1;
+    p->leaf_bijection = MPHF_BIJECTION_ROTATION;
     p->max_value = MPHF_DEFAULT_MAX_VALUE;
     p->leaf_method = MPHF_LEAF_LOCKSTEP;
 }
@@ -207,10 +207,11 @@ const char *mphf_strerror(int code) {
     }
 }
 
-int mphf_tau_table(uint32_t leaf_size, uint32_t rotation_fitting, uint32_t max_m, uint8_t *h_out) {
-    if (!h_out || leaf_size < 2 || leaf_size > MPHF_MAX_LEAF || max_m > MPHF_MAX_BUCKET)
+int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t max_m, uint8_t *h_out) {
+    if (!h_out || leaf_size < 2 || leaf_size > MPHF_MAX_LEAF || max_m > MPHF_MAX_BUCKET ||
+        leaf_bijection > MPHF_BIJECTION_SHOCKHASH)
         return MPHF_EINVAL;
-    const SizeTables &t = size_tables(leaf_size, rotation_fitting ? 1 : 0);
+    const SizeTables &t = size_tables(leaf_size, leaf_bijection);
     memcpy(h_out, t.tau, max_m + 1);
     return MPHF_OK;
 }
@@ -249,7 +250,8 @@ int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
     if (p->threads_per_block &&
         (p->threads_per_block % 32 || p->threads_per_block > 512 || p->threads_per_block < 64))
         return MPHF_EINVAL;
-    if (p->leaf_method > MPHF_LEAF_TABLE) return MPHF_EINVAL;
+    if (p->leaf_method > MPHF_LEAF_TABLE || p->leaf_bijection > MPHF_BIJECTION_SHOCKHASH)
+        return MPHF_EINVAL;
     return MPHF_OK;
 }
 
@@ -403,7 +405,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         d.status = j.small;
         d.max_value = j.maxv;
         d.leaf = j.p.leaf_size;
-        d.rotation = j.p.rotation_fitting ? 1 : 0;
+        d.bij = j.p.leaf_bijection;
         d.nb = (uint32_t)j.nb;
         d.k30 = 1u << 2;
         d.k27 = 1u << 5;
@@ -458,7 +460,8 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         if (j.rc) continue;
         mphf_t *h = j.h;
         CU(cudaMemsetAsync(h->bit_pos, 0, (j.nb + 1) * 8, st));
-        launch_gr_lengths(h->values, j.node_m, h->node_off, j.nb, h->tabs.tau, h->bit_pos, st);
+        launch_gr_lengths(h->values, j.node_m, h->node_off, j.nb, h->tabs.tau, j.p.leaf_size,
+                          j.p.leaf_bijection, h->bit_pos, st);
         launch_exclusive_scan(h->bit_pos, j.nb + 1, scan_tmp, st);
         CU(cudaGetLastError());
         CU(cudaMemcpyAsync(host + 4 * i, h->bit_pos + j.nb, 8, cudaMemcpyDeviceToHost, st));
@@ -500,15 +503,14 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         CU(cudaMemsetAsync(h->gr, 0, h->info.gr_words * 8 + 8, st));
         CU(cudaMemsetAsync(h->ef, 0, h->info.ef_words * 8 + 8, st));
         launch_gr_write(h->values, j.node_m, h->node_off, h->bit_pos, j.nb, h->tabs.tau,
-                        h->tabs.fixed, h->cum_keys, h->gr, st);
+                        h->tabs.fixed, h->cum_keys, j.p.leaf_size, j.p.leaf_bijection, h->gr, st);
         uint64_t *lo0 = h->ef, *hi0 = lo0 + e0.low_words, *lo1 = hi0 + e0.high_words,
                  *hi1 = lo1 + e1.low_words;
         launch_ef_write(h->cum_keys, j.nb + 1, e0.L, lo0, hi0, st);
         launch_ef_write(h->bit_pos, j.nb + 1, e1.L, lo1, hi1, st);
         launch_rank_dir(hi0, e0.high_words, h->ef_dir, scan_tmp, st);
         launch_rank_dir(hi1, e1.high_words, h->ef_dir + h->ef_dir_len[0], scan_tmp, st);
-        launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.rotation_fitting ? 1 : 0,
-                     j.counters, st);
+        launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.leaf_bijection, j.counters, st);
         CU(cudaGetLastError());
     }
     cudaEventRecord(ev[4], st);
@@ -579,8 +581,8 @@ void start_job(Job &j, const void *d_keys, uint64_t n, const mphf_build_params &
     h->info.leaf_size = p.leaf_size;
     h->info.bucket_size = p.bucket_size;
     h->info.key_bytes = p.key_bytes;
-    h->info.rotation_fitting = p.rotation_fitting ? 1 : 0;
-    int rc = device_tables(h->device, p.leaf_size, h->info.rotation_fitting, &h->tabs);
+    h->info.leaf_bijection = p.leaf_bijection;
+    int rc = device_tables(h->device, p.leaf_size, h->info.leaf_bijection, &h->tabs);
     if (rc) {
         release(h);
         j.h = nullptr;
@@ -652,7 +654,7 @@ static QueryView view_of(const mphf_t *h) {
     q.fixed_tab = h->tabs.fixed;
     q.nb = I.nb;
     q.leaf = I.leaf_size;
-    q.rotation = I.rotation_fitting;
+    q.bij = I.leaf_bijection;
     q.key_bytes = I.key_bytes;
     q.pad = 0;
     return q;
@@ -745,7 +747,7 @@ int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream) {
     }
     uint64_t hd[16] = {0x3130485046504D52ull /* "RMPHF01" */, h->info.n, h->info.nb,
                        h->info.leaf_size, h->info.bucket_size, h->info.key_bytes,
-                       h->info.rotation_fitting, h->info.gr_bits, h->info.gr_words,
+                       h->info.leaf_bijection, h->info.gr_bits, h->info.gr_words,
                        h->info.ef_words, h->info.ef_low_bits[0], h->info.ef_low_bits[1],
                        h->info.ef_seq_words[0], h->info.ef_seq_words[1], h->info.ef_seq_words[2],
                        h->info.ef_seq_words[3]};
@@ -782,7 +784,7 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
         p.leaf_size = descs[i].leaf_size;
         p.bucket_size = descs[i].bucket_size;
         p.key_bytes = descs[i].key_bytes;
-        p.rotation_fitting = descs[i].rotation_fitting;
+        p.leaf_bijection = descs[i].leaf_bijection;
         p.max_value = descs[i].max_value ? descs[i].max_value : MPHF_DEFAULT_MAX_VALUE;
         outs[i] = nullptr;
         start_job(jobs[i], descs[i].d_keys, descs[i].n, p);
@@ -888,7 +890,7 @@ static void server_worker(mphf_server_t *S, int w) {
             p.leaf_size = d.leaf_size;
             p.bucket_size = d.bucket_size;
             p.key_bytes = d.key_bytes;
-            p.rotation_fitting = d.rotation_fitting;
+            p.leaf_bijection = d.leaf_bijection;
             p.max_value = d.max_value ? d.max_value : MPHF_DEFAULT_MAX_VALUE;
             start_job(jobs[i], d.d_keys, d.n, p);
         }

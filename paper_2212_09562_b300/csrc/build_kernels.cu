@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "engine.h"
+#include "mphf.h"
 
 namespace rs {
 
@@ -737,6 +738,159 @@ __device__ __forceinline__ uint64_t leaf_cyclic(const uint64_t *xs, const uint8_
 }
 
 // Any two equal lo words among keys [0, m) of the block's bucket.
+// ShockHash leaf (Appendix C), one warp per leaf and one seed per round.
+// Lane i < m hashes key i to its two cells c0 = lo32(h) mod m and
+// c1 = hi32(h) mod m.  The keys are the edges of a multigraph on the m
+// cells; a bijection choosing one cell per key exists iff no component gets
+// more keys than cells.  Lane c holds the cell mask of cell c's component and
+// `cyc` the cells of components that already hold their one cycle, so every
+// edge is a few warp-uniform shuffles and the round stops at the first
+// component that would get a second cycle.  An accepted graph gets its
+// canonical bits (leaf_shock_bits) and its retrieval vector
+// (leaf_shock_solve); the smallest seed with both is stored with the vector
+// in bits MPHF_SH_BITS and up.
+__device__ __forceinline__ uint32_t leaf_shock_bits(uint32_t c0, uint32_t c1, uint64_t lo, uint32_t m,
+                                                    uint32_t lane) {
+    const bool key = lane < m;
+    uint32_t deg = 0;  // lane = cell
+    for (uint32_t i = 0; i < m; i++) {
+        const uint32_t u = __shfl_sync(0xffffffffu, c0, i), v = __shfl_sync(0xffffffffu, c1, i);
+        deg += (u == lane) + (v == lane);
+    }
+    bool alive = key;  // lane = key
+    uint32_t beta = 0;
+    // trees: a cell of degree one takes its only remaining key
+    for (uint32_t it = 0; it < m; it++) {
+        const uint32_t ones = __ballot_sync(0xffffffffu, key && deg == 1);
+        if (!ones) break;
+        const uint32_t c = __ffs(ones) - 1;
+        const uint32_t eb = __ballot_sync(0xffffffffu, alive && (c0 == c || c1 == c));
+        if (!eb) break;
+        const uint32_t e = __ffs(eb) - 1;
+        const uint32_t ue = __shfl_sync(0xffffffffu, c0, e), ve = __shfl_sync(0xffffffffu, c1, e);
+        if (lane == e) {
+            beta = c0 == c ? 0u : 1u;
+            alive = false;
+        }
+        const uint32_t other = ue == c ? ve : ue;
+        if (lane == c) deg = 0;
+        if (lane == other) deg -= 1;
+    }
+    // cycles: walked from the key with the smallest lo word, which takes c0
+    for (uint32_t it = 0; it < m; it++) {
+        if (!__any_sync(0xffffffffu, alive)) break;
+        unsigned long long best = alive ? lo : ~0ull;
+        for (int d = 16; d; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, d);
+            best = o < best ? o : best;
+        }
+        const uint32_t e0 = __ffs(__ballot_sync(0xffffffffu, alive && lo == best)) - 1;
+        const uint32_t start = __shfl_sync(0xffffffffu, c0, e0);
+        uint32_t cur = __shfl_sync(0xffffffffu, c1, e0);
+        if (lane == e0) {
+            beta = 0;
+            alive = false;
+        }
+        for (uint32_t k = 0; k < m && cur != start; k++) {
+            const uint32_t eb = __ballot_sync(0xffffffffu, alive && (c0 == cur || c1 == cur));
+            if (!eb) break;
+            const uint32_t e = __ffs(eb) - 1;
+            const uint32_t ue = __shfl_sync(0xffffffffu, c0, e), ve = __shfl_sync(0xffffffffu, c1, e);
+            if (lane == e) {
+                beta = c0 == cur ? 0u : 1u;
+                alive = false;
+            }
+            cur = ue == cur ? ve : ue;
+        }
+    }
+    return beta;
+}
+
+// Gauss-Jordan over GF(2), lane i < m holding row i and its bit: columns in
+// increasing order, the lowest remaining lane with the column's bit as pivot.
+// The reduced row echelon form is unique, so the solution with zero
+// non-pivot coordinates does not depend on the order of the keys.
+__device__ __forceinline__ bool leaf_shock_solve(uint32_t row, uint32_t rhs, uint32_t m, uint32_t lane,
+                                                 uint32_t &z) {
+    const bool key = lane < m;
+    bool piv = false;
+    uint32_t pcol = 0;
+    for (uint32_t j = 0; j < m; j++) {
+        const uint32_t cand = __ballot_sync(0xffffffffu, key && !piv && ((row >> j) & 1));
+        if (!cand) continue;
+        const uint32_t p = __ffs(cand) - 1;
+        const uint32_t rp = __shfl_sync(0xffffffffu, row, p), bp = __shfl_sync(0xffffffffu, rhs, p);
+        if (lane != p && ((row >> j) & 1)) {
+            row ^= rp;
+            rhs ^= bp;
+        }
+        if (lane == p) {
+            piv = true;
+            pcol = j;
+        }
+    }
+    if (__any_sync(0xffffffffu, key && !piv && rhs)) return false;
+    z = __reduce_or_sync(0xffffffffu, (piv && rhs) ? (1u << pcol) : 0u);
+    return true;
+}
+
+template <uint32_t MT>
+__device__ __forceinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *los, uint32_t m_rt,
+                                               const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
+    const uint32_t m = MT ? MT : m_rt;
+    const bool key = lane < m;
+    const uint64_t x = key ? xs[lane] : 0;   // lo + salt(0)
+    const uint64_t lo = key ? los[lane] : 0;
+    const uint64_t row_salt = level_salt(MPHF_SH_ROW_LEVEL);
+    const ModRT mod = make_mod(m);
+    if (maxv > MPHF_SH_MASK) maxv = MPHF_SH_MASK;
+    for (uint64_t s = 0;; s++) {
+        uint32_t hl, hh;
+        mx(x + s, hl, hh);
+        uint32_t c0, c1;
+        if constexpr (MT != 0) {
+            c0 = hl % MT;
+            c1 = hh % MT;
+        } else {
+            c0 = mod32(mod, hl);
+            c1 = mod32(mod, hh);
+        }
+        uint32_t cm = 1u << lane, cyc = 0;
+        bool ok = true;
+        for (uint32_t i = 0; i < m; i++) {
+            const uint32_t u = __shfl_sync(0xffffffffu, c0, i), v = __shfl_sync(0xffffffffu, c1, i);
+            const uint32_t mu = __shfl_sync(0xffffffffu, cm, u);
+            if ((mu >> v) & 1) {  // both cells in one component: it closes its cycle
+                if (cyc & mu) {
+                    ok = false;
+                    break;
+                }
+                cyc |= mu;
+            } else {
+                const uint32_t mv = __shfl_sync(0xffffffffu, cm, v);
+                if ((cyc & mu) && (cyc & mv)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t mm = mu | mv;
+                if (cyc & mm) cyc |= mm;
+                if ((mm >> lane) & 1) cm = mm;
+            }
+        }
+        if (ok) {
+            const uint32_t beta = leaf_shock_bits(c0, c1, lo, m, lane);
+            const uint64_t r = mix64(lo + row_salt + s);
+            const uint32_t row = key ? ((uint32_t)r & ((1u << m) - 1)) : 0u;
+            uint32_t z;
+            if (leaf_shock_solve(row, key ? beta : 0u, m, lane, z)) return s | ((uint64_t)z << MPHF_SH_BITS);
+        }
+        if (s >= maxv) {
+            limit = true;
+            return 0;
+        }
+    }
+}
+
 __device__ __forceinline__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
     bool dup = false;
     for (uint32_t i = threadIdx.x; i < m && !dup; i += blockDim.x)
@@ -887,18 +1041,26 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
         bool limit = false;
         uint64_t x;
         bool done = false;
-        if (d.leaf_method == 0) {  // lock-step: every lane hashes all m keys per trial
+        if (d.bij == MPHF_BIJECTION_SHOCKHASH) {
+            if constexpr (LEAF != 0) {
+                if (m == (uint32_t)LEAF) {
+                    x = leaf_shock<LEAF>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
+                    done = true;
+                }
+            }
+            if (!done) x = leaf_shock<0>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
+        } else if (d.leaf_method == 0) {  // lock-step: every lane hashes all m keys per trial
             uint32_t bmask = 0;
             for (uint32_t i = 0; i < m; i++) bmask |= (uint32_t)A.bb[off + i] << i;
             if constexpr (LEAF != 0) {
                 if (m == (uint32_t)LEAF) {  // full leaf: compile-time m and modulus
-                    x = d.rotation ? leaf_rotation<LEAF>(xs, bmask, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
+                    x = d.bij ? leaf_rotation<LEAF>(xs, bmask, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
                                    : leaf_plain<LEAF>(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
                     done = true;
                 }
             }
             if (!done)
-                x = d.rotation ? leaf_rotation<0>(xs, bmask, m, make_mod(m), mx, d.max_value, limit, lane)
+                x = d.bij ? leaf_rotation<0>(xs, bmask, m, make_mod(m), mx, d.max_value, limit, lane)
                                : leaf_plain<0>(xs, m, make_mod(m), mx, d.max_value, limit, lane);
         } else {  // early rejection (1), with the rotation lookup table (2)
             const bool use_lut = d.leaf_method == 2 && m <= 16 && d.rot_canon;
@@ -906,13 +1068,13 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
             const uint8_t *period = use_lut ? d.rot_period + ((1u << m) - 4) : nullptr;
             if constexpr (LEAF != 0) {
                 if (m == (uint32_t)LEAF) {
-                    x = d.rotation ? leaf_cyclic<true>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, canon, period)
+                    x = d.bij ? leaf_cyclic<true>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, canon, period)
                                    : leaf_cyclic<false>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, nullptr, nullptr);
                     done = true;
                 }
             }
             if (!done)
-                x = d.rotation ? leaf_cyclic<true>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, canon, period)
+                x = d.bij ? leaf_cyclic<true>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, canon, period)
                                : leaf_cyclic<false>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, nullptr, nullptr);
         }
         if (lane == 0) {
@@ -1046,16 +1208,36 @@ void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t ite
 
 // ---------------------------------------------------------------------------
 // Golomb-Rice: per-bucket lengths, then the bits (one warp per bucket).
+// A node codes its value with its size's parameter tau; a ShockHash leaf
+// codes its seed and appends its m-bit retrieval vector to the fixed part.
+struct GrPiece {
+    uint64_t fixed;  // fixed-part bits, LSB first
+    uint32_t width;  // their number
+    uint64_t high;   // unary part: zeros before the one
+};
+__device__ __forceinline__ GrPiece gr_piece(uint64_t v, uint32_t m, uint32_t t, uint32_t leaf, uint32_t bij) {
+    GrPiece g;
+    const bool shock = bij == MPHF_BIJECTION_SHOCKHASH && m <= leaf;
+    const uint64_t coded = shock ? (v & MPHF_SH_MASK) : v;
+    const uint64_t low = t ? (coded & ((t == 64) ? ~0ull : ((1ull << t) - 1))) : 0;
+    g.fixed = shock ? (low | ((v >> MPHF_SH_BITS) << t)) : low;
+    g.width = shock ? t + m : t;
+    g.high = coded >> t;
+    return g;
+}
+
 __global__ void k_gr_len(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
-                         uint64_t nb, const uint8_t *tau, uint64_t *bucket_bits) {
+                         uint64_t nb, const uint8_t *tau, uint32_t leaf, uint32_t bij,
+                         uint64_t *bucket_bits) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t b = warp; b < nb; b += nwarps) {
         uint64_t bits = 0;
         for (uint64_t j = node_off[b] + lane; j < node_off[b + 1]; j += 32) {
-            uint32_t t = tau[node_m[j]];
-            bits += t + 1 + (values[j] >> t);
+            const uint32_t m = node_m[j];
+            const GrPiece g = gr_piece(values[j], m, tau[m], leaf, bij);
+            bits += g.width + 1 + g.high;
         }
         for (int d = 16; d; d >>= 1) bits += __shfl_xor_sync(0xffffffffu, bits, d);
         if (lane == 0) bucket_bits[b] = bits;
@@ -1063,9 +1245,11 @@ __global__ void k_gr_len(const uint64_t *values, const uint16_t *node_m, const u
 }
 
 void launch_gr_lengths(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
-                       uint64_t nb, const uint8_t *tau, uint64_t *bucket_bits, cudaStream_t st) {
+                       uint64_t nb, const uint8_t *tau, uint32_t leaf, uint32_t bij,
+                       uint64_t *bucket_bits, cudaStream_t st) {
     if (nb == 0) return;
-    k_gr_len<<<grid_for(nb * 32, 256), 256, 0, st>>>(values, node_m, node_off, nb, tau, bucket_bits);
+    k_gr_len<<<grid_for(nb * 32, 256), 256, 0, st>>>(values, node_m, node_off, nb, tau, leaf, bij,
+                                                       bucket_bits);
     note_launches(1);
 }
 
@@ -1078,7 +1262,8 @@ __device__ __forceinline__ void or_bits(uint64_t *w, uint64_t pos, uint64_t v, u
 
 __global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                            const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
-                           const uint32_t *fixed_tab, const uint64_t *bucket_off, uint64_t *gr) {
+                           const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
+                           uint32_t bij, uint64_t *gr) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -1090,13 +1275,15 @@ __global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const
         for (uint64_t j0 = node_off[b]; j0 < node_off[b + 1]; j0 += 32) {
             const uint64_t j = j0 + lane;
             const bool valid = j < node_off[b + 1];
-            const uint32_t t = valid ? tau[node_m[j]] : 0;
-            const uint64_t x = valid ? values[j] : 0;
-            const uint64_t ulen = valid ? (x >> t) + 1 : 0;
-            const uint64_t it = warp_incl_scan(t), iu = warp_incl_scan(ulen);
+            GrPiece g{0, 0, 0};
             if (valid) {
-                uint64_t fx = t ? (x & ((t == 64) ? ~0ull : ((1ull << t) - 1))) : 0;
-                or_bits(gr, start + frun + it - t, fx, t);
+                const uint32_t mj = node_m[j];
+                g = gr_piece(values[j], mj, tau[mj], leaf, bij);
+            }
+            const uint64_t ulen = valid ? g.high + 1 : 0;
+            const uint64_t it = warp_incl_scan(g.width), iu = warp_incl_scan(ulen);
+            if (valid) {
+                or_bits(gr, start + frun + it - g.width, g.fixed, g.width);
                 uint64_t up = ustart + urun + iu - 1;
                 atomicOr((unsigned long long *)&gr[up >> 6], 1ull << (up & 63));
             }
@@ -1108,11 +1295,11 @@ __global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const
 
 void launch_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                      const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
-                     const uint32_t *fixed_tab, const uint64_t *bucket_off, uint64_t *gr,
-                     cudaStream_t st) {
+                     const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
+                     uint32_t bij, uint64_t *gr, cudaStream_t st) {
     if (nb == 0) return;
     k_gr_write<<<grid_for(nb * 32, 256), 256, 0, st>>>(values, node_m, node_off, bit_pos, nb, tau,
-                                                         fixed_tab, bucket_off, gr);
+                                                         fixed_tab, bucket_off, leaf, bij, gr);
     note_launches(1);
 }
 
@@ -1146,7 +1333,7 @@ __global__ void k_popcount(const uint64_t *words, uint64_t n, uint64_t *out) {
 
 // Stats: trials up to the stored value, and hash evaluations, per node kind.
 __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes,
-                        uint32_t leaf, uint32_t rotation, unsigned long long *counters) {
+                        uint32_t leaf, uint32_t bij, unsigned long long *counters) {
     __shared__ unsigned long long acc[8];
     if (threadIdx.x < 8) acc[threadIdx.x] = 0;
     __syncthreads();
@@ -1156,7 +1343,9 @@ __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t
         uint32_t m = node_m[j];
         uint32_t kind = node_kind(sh, m);
         uint64_t x = values[j];
-        uint64_t trials = (kind == NODE_LEAF && rotation) ? x / m + 1 : x + 1;
+        uint64_t trials = x + 1;
+        if (kind == NODE_LEAF && bij == MPHF_BIJECTION_ROTATION) trials = x / m + 1;
+        if (kind == NODE_LEAF && bij == MPHF_BIJECTION_SHOCKHASH) trials = (x & MPHF_SH_MASK) + 1;
         uint32_t idx = kind == NODE_LEAF ? 0 : kind == NODE_LOWER1 ? 1 : kind == NODE_LOWER2 ? 2 : 3;
         atomicAdd(&acc[idx], (unsigned long long)trials);
         atomicAdd(&acc[4 + idx], (unsigned long long)(trials * m));
@@ -1166,9 +1355,9 @@ __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t
 }
 
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
-                  uint32_t rotation, uint64_t *counters, cudaStream_t st) {
+                  uint32_t bij, uint64_t *counters, cudaStream_t st) {
     if (n_nodes == 0) return;
-    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, leaf, rotation,
+    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, leaf, bij,
                                                           (unsigned long long *)counters);
     note_launches(1);
 }

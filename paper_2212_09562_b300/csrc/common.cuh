@@ -15,6 +15,11 @@
 
 #define MPHF_GOLDEN 0x9E3779B97F4A7C15ull
 #define MPHF_MAX_LEVELS 64
+// ShockHash leaves (Appendix C): seed in the low 40 bits of the stored word,
+// the retrieval vector above; retrieval rows hashed with the salt of level 63.
+#define MPHF_SH_BITS 40
+#define MPHF_SH_MASK ((1ull << MPHF_SH_BITS) - 1)
+#define MPHF_SH_ROW_LEVEL 63u
 
 namespace rs {
 
@@ -134,6 +139,12 @@ __host__ __device__ __forceinline__ ModRT make_mod(uint32_t m) {
     r.c = (uint32_t)((1ull << 32) % m);
     r.M = 0xFFFFFFFFFFFFFFFFull / m + 1;
     return r;
+}
+
+// ShockHash cells of a key: the two 32-bit halves of h, each mod m (Lemire,
+// Kaser and Kurz's direct remainder, exact for 32-bit values).
+__host__ __device__ __forceinline__ uint32_t mod32(const ModRT &r, uint32_t v) {
+    return (uint32_t)mulhi64(r.M * v, r.m);
 }
 
 // Compile-time modulus: same reduction, the last step by the compiler's

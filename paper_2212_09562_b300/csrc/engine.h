@@ -20,7 +20,7 @@ struct InstDesc {
     uint16_t *node_m;            // node sizes, same order
     uint32_t *status;            // ST_* bits
     uint64_t max_value;
-    uint32_t leaf, rotation;
+    uint32_t leaf, bij;          // bij: MPHF_BIJECTION_* leaf method
     uint32_t nb;
     uint32_t k30, k27, k31;      // 4, 32, 2: multipliers of the hash's xor-shifts
     uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
@@ -74,19 +74,22 @@ void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads, uint32_t blocks_per_sm);
 void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
                    const SearchLaunch &L, cudaStream_t st);
+// Golomb-Rice coding of the stored values (a ShockHash leaf codes its seed
+// and appends its retrieval vector to the fixed part).
 void launch_gr_lengths(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
-                       uint64_t nb, const uint8_t *tau, uint64_t *bucket_bits, cudaStream_t st);
+                       uint64_t nb, const uint8_t *tau, uint32_t leaf, uint32_t bij,
+                       uint64_t *bucket_bits, cudaStream_t st);
 void launch_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                      const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
-                     const uint32_t *fixed_tab, const uint64_t *bucket_off, uint64_t *gr,
-                     cudaStream_t st);
+                     const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
+                     uint32_t bij, uint64_t *gr, cudaStream_t st);
 void launch_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low, uint64_t *high,
                      cudaStream_t st);
 // dir[w] = ones in words [0, w), w in [0, nwords]; tmp: scan_tmp_words(nwords + 1).
 void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint64_t *tmp,
                      cudaStream_t st);
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
-                  uint32_t rotation, uint64_t *counters, cudaStream_t st);
+                  uint32_t bij, uint64_t *counters, cudaStream_t st);
 
 // Query side.
 struct QueryView {
@@ -98,7 +101,7 @@ struct QueryView {
     const uint8_t *tau;
     const uint32_t *nodes_tab, *fixed_tab;
     uint64_t nb;
-    uint32_t leaf, rotation, key_bytes, pad;
+    uint32_t leaf, bij, key_bytes, pad;
 };
 void launch_query(const QueryView &q, const void *keys, uint64_t n, uint64_t *out, cudaStream_t st);
 void launch_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad,

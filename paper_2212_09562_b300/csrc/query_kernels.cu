@@ -6,12 +6,14 @@
 // part found by select in its unary region), hash to the child, add the
 // sizes of the children to its left and skip their subtrees (per-size
 // tables give their node counts and fixed bits).  At the leaf: the position
-// under the leaf's seed, plus the rotation r mod m for keys of B (Section 4).
+// under the leaf's seed, plus the rotation r mod m for keys of B (Section 4),
+// or the retrieved one of the key's two cells (ShockHash, Appendix C).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "common.cuh"
 #include "engine.h"
+#include "mphf.h"
 
 namespace rs {
 
@@ -113,8 +115,16 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
         uint64_t x = node_value(q.gr, fpos, q.tau[m], ustart, idx);
         const ModRT mod = make_mod(m);
         uint64_t pos;
-        if (!q.rotation) {
+        if (q.bij == MPHF_BIJECTION_PLAIN) {
             pos = mod(mix64(lo + level_salt(0) + x));
+        } else if (q.bij == MPHF_BIJECTION_SHOCKHASH) {
+            // Appendix C: the retrieval vector follows the seed's tau bits;
+            // parity(row & Z) says which of its two cells the key occupies
+            const uint32_t z = (uint32_t)read_bits(q.gr, fpos + q.tau[m], m);
+            const uint64_t h = mix64(lo + level_salt(0) + x);
+            const uint32_t row = (uint32_t)mix64(lo + level_salt(MPHF_SH_ROW_LEVEL) + x) & ((1u << m) - 1);
+            const uint32_t half = (__popc(row & z) & 1) ? (uint32_t)(h >> 32) : (uint32_t)h;
+            pos = mod32(mod, half);
         } else {
             uint64_t r = x % m;
             pos = mod(mix64(lo + level_salt(0) + (x - r)));

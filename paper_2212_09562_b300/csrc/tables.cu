@@ -1,4 +1,4 @@
-// tables.cpp -- Golomb-Rice parameters and subtree sizes per node size.
+// tables.cu -- Golomb-Rice parameters and subtree sizes per node size.
 //
 // Section 2.2 ("Representation") stores the node values with Golomb-Rice
 // codes whose parameter depends on the layer and is precomputed.  The
@@ -11,6 +11,10 @@
 //   rotation-fitting leaf:           (Appendix A lemma bound, averaged over
 //                                     |A| ~ Binomial(m, 1/2)) / m, since one
 //                                     seed k*m covers m stored values.
+//   ShockHash leaf (Appendix C):     P(the two cells of the m keys admit a
+//                                     bijection) * P(the m x m GF(2)
+//                                     retrieval system is solvable).
+// A ShockHash leaf's fixed part also holds its m retrieval bits.
 #include "tables.h"
 
 #include <math.h>
@@ -19,6 +23,9 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <vector>
+
+#include "mphf.h"
 
 #include "common.cuh"
 
@@ -76,6 +83,52 @@ double split_success(const Shape &s, uint32_t m) {
     return exp(lg);
 }
 
+// Cuckoo graph of m keys on m cells, each key an edge between its two cells
+// (chosen uniformly, a loop when they agree).  A bijection exists iff every
+// component carries exactly one cycle.  Counting over labelled cells and
+// keys: pairs (edge list, bijective choice of one cell per key) number
+// k! 2^k k^k on k cells; a connected one-cycle list has two choices.  Split
+// off the component of the first cell (j cells of k, j keys of k):
+//   pairs(k)  = sum_j C(k-1, j-1) C(k, j) * 2 conn(j) * pairs(k - j)
+//   cycles(k) = sum_j C(k-1, j-1) C(k, j) * conn(j) * cycles(k - j)
+// and P = cycles(m) / m^(2m).
+double shock_bijection_prob(uint32_t m) {
+    std::vector<double> pairs(m + 1), conn(m + 1), cycles(m + 1);
+    pairs[0] = 1.0;
+    cycles[0] = 1.0;
+    for (uint32_t k = 1; k <= m; k++) {
+        double w = 1.0;
+        for (uint32_t i = 1; i <= k; i++) w *= 2.0 * (double)i * (double)k;
+        pairs[k] = w;
+        double other = 0.0, acc = 0.0;
+        for (uint32_t j = 1; j < k; j++) {
+            const double ways = choose(k - 1, j - 1) * choose(k, j);
+            other += ways * 2.0 * conn[j] * pairs[k - j];
+            acc += ways * conn[j] * cycles[k - j];
+        }
+        conn[k] = (pairs[k] - other) / 2.0;
+        cycles[k] = acc + conn[k];
+    }
+    return cycles[m] / pow((double)m, 2.0 * (double)m);
+}
+
+// A fixed nonzero right-hand side against m uniform random rows of m bits:
+// solvable with probability sum_r P(rank r) (2^r - 1) / (2^m - 1), where
+// P(rank r) = 2^-((m-r)^2) prod_{i<r} (1 - 2^(i-m))^2 / (1 - 2^(i-r)).
+double gf2_solvable_prob(uint32_t m) {
+    double sum = 0.0;
+    for (uint32_t r = 0; r <= m; r++) {
+        const int d = (int)(m - r);
+        double pr = ldexp(1.0, -d * d);
+        for (uint32_t i = 0; i < r; i++) {
+            const double q = 1.0 - ldexp(1.0, (int)i - (int)m);
+            pr *= q * q / (1.0 - ldexp(1.0, (int)i - (int)r));
+        }
+        sum += pr * (ldexp(1.0, (int)r) - 1.0) / (ldexp(1.0, (int)m) - 1.0);
+    }
+    return sum;
+}
+
 uint8_t kiely(double p) {
     const double phi = (1.0 + sqrt(5.0)) / 2.0;
     double k = 1.0 + floor(log2(log(phi - 1.0) / log1p(-p)));
@@ -84,36 +137,40 @@ uint8_t kiely(double p) {
 
 }  // namespace
 
-uint8_t node_tau(uint32_t leaf, uint32_t rotation, uint32_t m) {
+uint8_t node_tau(uint32_t leaf, uint32_t bij, uint32_t m) {
     if (m < 2) return 0;
     Shape s = make_shape(leaf);
     double p;
-    if (m <= leaf)
-        p = rotation ? rotation_leaf_success(m) / (double)m : all_distinct(m, m);
-    else
+    if (m > leaf)
         p = split_success(s, m);
+    else if (bij == MPHF_BIJECTION_ROTATION)
+        p = rotation_leaf_success(m) / (double)m;
+    else if (bij == MPHF_BIJECTION_SHOCKHASH)
+        p = shock_bijection_prob(m) * gf2_solvable_prob(m);
+    else
+        p = all_distinct(m, m);
     return kiely(p);
 }
 
-const SizeTables &size_tables(uint32_t leaf, uint32_t rotation) {
+const SizeTables &size_tables(uint32_t leaf, uint32_t bij) {
     static std::mutex mu;
     static std::map<uint32_t, std::unique_ptr<SizeTables>> cache;
     std::lock_guard<std::mutex> g(mu);
-    uint32_t key = leaf * 2 + (rotation ? 1 : 0);
+    uint32_t key = leaf * 4 + bij;
     auto it = cache.find(key);
     if (it != cache.end()) return *it->second;
     auto t = std::make_unique<SizeTables>();
     t->leaf = leaf;
-    t->rotation = rotation ? 1 : 0;
+    t->bij = bij;
     Shape s = make_shape(leaf);
     for (uint32_t m = 0; m <= 4096; m++) {
-        t->tau[m] = node_tau(leaf, rotation, m);
+        t->tau[m] = node_tau(leaf, bij, m);
         if (m < 2) {
             t->nodes[m] = 0;
             t->fixed[m] = 0;
         } else if (m <= leaf) {
             t->nodes[m] = 1;
-            t->fixed[m] = t->tau[m];
+            t->fixed[m] = t->tau[m] + (bij == MPHF_BIJECTION_SHOCKHASH ? m : 0);
         } else {
             uint32_t nodes = 1, fixed = t->tau[m];
             for (uint32_t c = 0, np = num_parts(s, m); c < np; c++) {

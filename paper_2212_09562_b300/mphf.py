@@ -31,6 +31,17 @@ MAX_BUCKET = 4096
 VERIFY_STATIC_MAX_KEYS = 1 << 20
 DEFAULT_MAX_VALUE = (1 << 40) - 1
 LEAF_LOCKSTEP, LEAF_EARLY, LEAF_TABLE = 0, 1, 2
+# leaf bijection methods; every ``rotation`` argument takes a bool or one of these
+PLAIN, ROTATION, SHOCKHASH = 0, 1, 2
+SH_SEED_BITS = 40  # a ShockHash leaf's value: seed below bit 40, retrieval vector above
+
+
+def bijection(rotation) -> int:
+    """MPHF_BIJECTION_* code from a bool (rotation fitting on/off) or PLAIN/ROTATION/SHOCKHASH."""
+    v = int(rotation)
+    if v not in (PLAIN, ROTATION, SHOCKHASH):
+        raise ValueError(f"unknown leaf method {rotation!r}")
+    return v
 
 _lock = threading.Lock()
 _lib = None
@@ -49,7 +60,7 @@ class Allocator(ctypes.Structure):
 
 class BuildParams(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_uint32), ("bucket_size", ctypes.c_uint32),
-                ("key_bytes", ctypes.c_uint32), ("rotation_fitting", ctypes.c_uint32),
+                ("key_bytes", ctypes.c_uint32), ("leaf_bijection", ctypes.c_uint32),
                 ("max_value", ctypes.c_uint64), ("allocator", ctypes.c_void_p),
                 ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("leaf_method", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
@@ -58,7 +69,7 @@ class BuildParams(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("nb", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
                 ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
-                ("rotation_fitting", ctypes.c_uint32), ("n_nodes", ctypes.c_uint64),
+                ("leaf_bijection", ctypes.c_uint32), ("n_nodes", ctypes.c_uint64),
                 ("gr_bits", ctypes.c_uint64), ("gr_words", ctypes.c_uint64),
                 ("ef_words", ctypes.c_uint64), ("ef_low_bits", ctypes.c_uint32 * 2),
                 ("ef_seq_words", ctypes.c_uint64 * 4), ("max_bucket", ctypes.c_uint32),
@@ -84,7 +95,7 @@ class RequestTimes(ctypes.Structure):
 class BuildDesc(ctypes.Structure):
     _fields_ = [("d_keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
                 ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
-                ("rotation_fitting", ctypes.c_uint32), ("max_value", ctypes.c_uint64)]
+                ("leaf_bijection", ctypes.c_uint32), ("max_value", ctypes.c_uint64)]
 
 
 # Every entry point of include/mphf.h: name -> (restype, argtypes)
@@ -197,11 +208,12 @@ class MPHF:
 
     # --- construction -------------------------------------------------------
     @classmethod
-    def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation: bool = True,
+    def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
               max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
               blocks_per_sm: int = 0, stream=None, tuned: bool = False,
               leaf_method: int | None = None) -> "MPHF":
-        """tuned=True takes the launch shape from the autotuner's cache;
+        """rotation: True/False or PLAIN, ROTATION, SHOCKHASH (the leaf method);
+        tuned=True takes the launch shape from the autotuner's cache;
         leaf_method: LEAF_LOCKSTEP (default), LEAF_EARLY or LEAF_TABLE."""
         n, kb = key_layout(keys)
         if tuned and not threads_per_block and not blocks_per_sm:
@@ -209,7 +221,7 @@ class MPHF:
             threads_per_block, blocks_per_sm = cached_shape(leaf_size, rotation)
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
-        p.rotation_fitting = 1 if rotation else 0
+        p.leaf_bijection = bijection(rotation)
         p.max_value = max_value
         p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
         if leaf_method is not None:
@@ -222,14 +234,14 @@ class MPHF:
 
     @classmethod
     def build_host(cls, keys: np.ndarray, leaf_size: int = 16, bucket_size: int = 2000,
-                   rotation: bool = True, max_value: int = DEFAULT_MAX_VALUE,
+                   rotation=True, max_value: int = DEFAULT_MAX_VALUE,
                    stream=None) -> "MPHF":
         """Build from keys in host memory (copied to the device inside the call)."""
         keys = np.ascontiguousarray(keys)
         kb = 8 if keys.ndim == 1 else 16
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
-        p.rotation_fitting = 1 if rotation else 0
+        p.leaf_bijection = bijection(rotation)
         p.max_value = max_value
         h = ctypes.c_void_p()
         rc = lib().mphf_build_host(keys.ctypes.data if len(keys) else None, len(keys),
@@ -325,14 +337,14 @@ def kernel_launches() -> int:
     return int(lib().mphf_kernel_launches())
 
 
-def tau_table(leaf_size: int, rotation: bool, max_m: int = MAX_BUCKET) -> np.ndarray:
+def tau_table(leaf_size: int, rotation, max_m: int = MAX_BUCKET) -> np.ndarray:
     out = np.zeros(max_m + 1, np.uint8)
-    _check(lib().mphf_tau_table(leaf_size, 1 if rotation else 0, max_m, out.ctypes.data),
+    _check(lib().mphf_tau_table(leaf_size, bijection(rotation), max_m, out.ctypes.data),
            "mphf_tau_table")
     return out
 
 
-def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation: bool = True,
+def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation=True,
                 max_value: int = 0, stream=None) -> list[MPHF]:
     """Many independent builds in one call (see mphf_build_batch)."""
     count = len(keys_list)
@@ -340,7 +352,7 @@ def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation: bool =
     for i, (k, l) in enumerate(zip(keys_list, leaf_sizes)):
         n, kb = key_layout(k)
         descs[i] = BuildDesc(k.data_ptr() if n else None, n, l, bucket_size, kb,
-                             1 if rotation else 0, max_value)
+                             bijection(rotation), max_value)
     outs = (ctypes.c_void_p * max(count, 1))()
     sts = (ctypes.c_int * max(count, 1))()
     rc = lib().mphf_build_batch(descs, count, _stream(stream), outs, sts)
@@ -363,11 +375,11 @@ class Server:
         self._h = h
         self._keep = {}  # ticket -> key tensor, alive until the request is polled
 
-    def submit(self, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation: bool = True,
+    def submit(self, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
                max_value: int = 0) -> int:
         n, kb = key_layout(keys)
         d = BuildDesc(keys.data_ptr() if n else None, n, leaf_size, bucket_size, kb,
-                      1 if rotation else 0, max_value)
+                      bijection(rotation), max_value)
         t = ctypes.c_uint64()
         _check(lib().mphf_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)),
                "mphf_server_submit")

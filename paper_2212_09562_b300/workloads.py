@@ -9,6 +9,8 @@ random 128-bit integers used directly, or random strings).  The workloads:
 * ``plain_l8``   n = 100,000 distinct uniform 64-bit keys, l = 8, b = 100, no rotation fitting
 * ``rot_l12``    n = 1,000,000 distinct uniform 16-byte keys, l = 12, b = 1000, rotation fitting
 * ``rot_l16``    n = 10,000,000 distinct uniform 64-bit keys, l = 16, b = 2000, rotation fitting
+* ``shock_l16``  the keys and shape of ``rot_l16`` (another seed) with ShockHash leaves
+  (Appendix C)
 * ``batch``      4,096 builds, n_i = floor(10^U(3,6)), l_i uniform in {8, 12, 16}, b = 2000
 * ``serve``      Poisson request stream, mean 200/s, n ~ floor(10^U(4,7)) 16-byte keys, l = 16
 """
@@ -28,7 +30,7 @@ class Workload:
     leaf: int
     bucket: int
     key_bytes: int
-    rotation: bool
+    rotation: int  # leaf method: 0 / False plain, 1 / True rotation fitting, 2 ShockHash
     seed: int
 
 
@@ -36,6 +38,7 @@ WORKLOADS = {
     "plain_l8": Workload("plain_l8", 100_000, 8, 100, 8, False, SEED_BASE + 1),
     "rot_l12": Workload("rot_l12", 1_000_000, 12, 1000, 16, True, SEED_BASE + 2),
     "rot_l16": Workload("rot_l16", 10_000_000, 16, 2000, 8, True, SEED_BASE + 3),
+    "shock_l16": Workload("shock_l16", 10_000_000, 16, 2000, 8, 2, SEED_BASE + 4),
 }
 
 

@@ -48,7 +48,7 @@ def test_error_strings(lib):
 
 def test_default_params(lib):
     p = M.default_params()
-    assert (p.leaf_size, p.bucket_size, p.key_bytes, p.rotation_fitting) == (16, 2000, 8, 1)
+    assert (p.leaf_size, p.bucket_size, p.key_bytes, p.leaf_bijection) == (16, 2000, 8, 1)
     assert p.max_value == M.DEFAULT_MAX_VALUE
 
 
@@ -56,16 +56,19 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     h = ctypes.c_void_p()
     p = M.default_params()
     for field, value in [("leaf_size", 1), ("leaf_size", 25), ("bucket_size", 0),
-                         ("bucket_size", 3001), ("key_bytes", 4), ("threads_per_block", 100)]:
+                         ("bucket_size", 3001), ("key_bytes", 4), ("threads_per_block", 100),
+                         ("leaf_bijection", 3), ("leaf_method", 3)]:
         q = M.default_params()
         setattr(q, field, value)
         assert lib.mphf_build_ex(None, 0, ctypes.byref(q), None, ctypes.byref(h)) == M.EINVAL
     assert lib.mphf_build_ex(None, 5, ctypes.byref(p), None, ctypes.byref(h)) == M.EINVAL
     assert lib.mphf_query(None, None, 0, None, None) == M.EINVAL
     assert lib.mphf_tau_table(1, 1, 10, None) == M.EINVAL
+    out = np.zeros(11, np.uint8)
+    assert lib.mphf_tau_table(8, 3, 10, out.ctypes.data) == M.EINVAL
 
 
 @pytest.mark.parametrize("leaf", [2, 3, 5, 7, 8, 10, 12, 16, 20, 24])
-@pytest.mark.parametrize("rotation", [False, True])
+@pytest.mark.parametrize("rotation", [M.PLAIN, M.ROTATION, M.SHOCKHASH])
 def test_tau_tables_equal_the_oracle(lib, orc, leaf, rotation):
     assert np.array_equal(M.tau_table(leaf, rotation), orc.tau_table(leaf, rotation))
