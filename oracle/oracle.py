@@ -35,6 +35,10 @@ ROTATION = 1
 SHOCKHASH = 2
 SH_SEED_BITS = 40          # a ShockHash leaf word: seed in bits 0..39, retrieval vector above
 SH_RETRIEVAL_LEVEL = 63    # salt level of the retrieval rows
+# tree shapes: RecSplit's two lower aggregation levels, or fanout 2 everywhere (Appendix C)
+TREE_RECSPLIT = 0
+TREE_FANOUT2 = 1
+_FANOUT2_FLAG = 0x100      # carried on the leaf size argument of the C functions
 STAT_KINDS = ("leaf", "lower1", "lower2", "upper")
 
 _lock = threading.Lock()
@@ -108,6 +112,12 @@ def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
 
 
+def _leaf(leaf: int, tree: int) -> int:
+    if tree not in (TREE_RECSPLIT, TREE_FANOUT2):
+        raise ValueError(f"unknown tree shape {tree!r}")
+    return leaf | (_FANOUT2_FLAG if tree == TREE_FANOUT2 else 0)
+
+
 def bij(rotation) -> int:
     """Leaf method code from a bool (rotation fitting on/off) or PLAIN/ROTATION/SHOCKHASH."""
     v = int(rotation)
@@ -143,21 +153,21 @@ def bucket_of(hi: int, nb: int) -> int:
     return int(lib().orc_bucket_of(hi, nb))
 
 
-def fanouts(leaf: int) -> tuple[int, int]:
+def fanouts(leaf: int, tree: int = TREE_RECSPLIT) -> tuple[int, int]:
     f1 = ctypes.c_uint32()
     f2 = ctypes.c_uint32()
-    lib().orc_fanouts(leaf, ctypes.addressof(f1), ctypes.addressof(f2))
+    lib().orc_fanouts(_leaf(leaf, tree), ctypes.addressof(f1), ctypes.addressof(f2))
     return f1.value, f2.value
 
 
-def parts(leaf: int, m: int) -> list[int]:
+def parts(leaf: int, m: int, tree: int = TREE_RECSPLIT) -> list[int]:
     out = np.zeros(16, np.uint32)
-    k = lib().orc_parts(leaf, m, _ptr(out))
+    k = lib().orc_parts(_leaf(leaf, tree), m, _ptr(out))
     return [int(v) for v in out[:k]]
 
 
-def count_nodes(leaf: int, m: int) -> int:
-    return int(lib().orc_count_nodes(leaf, m))
+def count_nodes(leaf: int, m: int, tree: int = TREE_RECSPLIT) -> int:
+    return int(lib().orc_count_nodes(_leaf(leaf, tree), m))
 
 
 def salt(level: int) -> int:
@@ -176,8 +186,8 @@ def plain_success(m: int) -> float:
     return float(lib().orc_plain_success(m))
 
 
-def split_success(leaf: int, m: int) -> float:
-    return float(lib().orc_split_success(leaf, m))
+def split_success(leaf: int, m: int, tree: int = TREE_RECSPLIT) -> float:
+    return float(lib().orc_split_success(_leaf(leaf, tree), m))
 
 
 def kiely_tau(p: float) -> int:
@@ -192,9 +202,9 @@ def retrieval_solvable_prob(m: int) -> float:
     return float(lib().orc_retrieval_solvable_prob(m))
 
 
-def tau_table(leaf: int, rotation, max_m: int = MAX_BUCKET) -> np.ndarray:
+def tau_table(leaf: int, rotation, max_m: int = MAX_BUCKET, tree: int = TREE_RECSPLIT) -> np.ndarray:
     out = np.zeros(max_m + 1, np.uint8)
-    lib().orc_tau_table(leaf, bij(rotation), max_m, _ptr(out))
+    lib().orc_tau_table(_leaf(leaf, tree), bij(rotation), max_m, _ptr(out))
     return out
 
 
@@ -247,10 +257,11 @@ class OracleError(RuntimeError):
 
 
 def build_mphf(keys: np.ndarray, leaf: int, bucket: int, rotation=True,
-               max_value: int = DEFAULT_MAX_VALUE, threads: int = 1) -> OracleMPHF:
+               max_value: int = DEFAULT_MAX_VALUE, threads: int = 1,
+               tree: int = TREE_RECSPLIT) -> OracleMPHF:
     k, kb = _key_bytes(keys)
     h = ctypes.c_void_p()
-    rc = lib().orc_build(_ptr(k), k.shape[0], kb, leaf, bucket, bij(rotation), max_value,
+    rc = lib().orc_build(_ptr(k), k.shape[0], kb, _leaf(leaf, tree), bucket, bij(rotation), max_value,
                          threads, ctypes.byref(h))
     if rc != OK:
         raise OracleError(rc)
@@ -258,7 +269,7 @@ def build_mphf(keys: np.ndarray, leaf: int, bucket: int, rotation=True,
 
 
 def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation, buckets: np.ndarray,
-                 max_value: int = DEFAULT_MAX_VALUE, threads: int = 1):
+                 max_value: int = DEFAULT_MAX_VALUE, threads: int = 1, tree: int = TREE_RECSPLIT):
     """Values of the listed buckets only: (values concatenated in list order,
     node count per listed bucket, stats dict)."""
     k, kb = _key_bytes(keys)
@@ -267,7 +278,7 @@ def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation, buckets: np
     cap = MAX_BUCKET * len(buckets)  # a bucket has fewer stored nodes than keys
     vals = np.zeros(max(cap, 1), np.uint64)
     st = np.zeros(8, np.uint64)
-    rc = lib().orc_build_sample(_ptr(k), k.shape[0], kb, leaf, bucket, bij(rotation),
+    rc = lib().orc_build_sample(_ptr(k), k.shape[0], kb, _leaf(leaf, tree), bucket, bij(rotation),
                                 max_value, threads, _ptr(buckets), len(buckets), _ptr(vals),
                                 _ptr(counts), _ptr(st))
     if rc != OK:
@@ -278,13 +289,13 @@ def build_sample(keys: np.ndarray, leaf: int, bucket: int, rotation, buckets: np
 
 
 def node_search(leaf: int, rotation, lo: np.ndarray, hi: np.ndarray | None = None,
-                depth: int = 0, max_value: int = DEFAULT_MAX_VALUE):
+                depth: int = 0, max_value: int = DEFAULT_MAX_VALUE, tree: int = TREE_RECSPLIT):
     """Search one node's value directly: returns (rc, value, trials, evals)."""
     lo = np.ascontiguousarray(lo, dtype=np.uint64)
     hi = np.zeros_like(lo) if hi is None else np.ascontiguousarray(hi, dtype=np.uint64)
     x = np.zeros(1, np.uint64)
     st = np.zeros(2, np.uint64)
-    rc = lib().orc_node_search(leaf, bij(rotation), _ptr(lo), _ptr(hi), len(lo), depth,
+    rc = lib().orc_node_search(_leaf(leaf, tree), bij(rotation), _ptr(lo), _ptr(hi), len(lo), depth,
                                max_value, _ptr(x), _ptr(st))
     return rc, int(x[0]), int(st[0]), int(st[1])
 

@@ -21,7 +21,11 @@
  *   R3  tree shape: leaves of l keys, lower aggregation fanouts
  *       f1 = max(2, ceil(0.35 l + 0.55)), f2 = max(2, ceil(0.21 l + 0.9)) in
  *       integer arithmetic, fanout 2 above with the left part a multiple of
- *       the lower-2 node size.
+ *       the lower-2 node size.  The fanout-2 tree of Appendix C (used there
+ *       with ShockHash leaves) has fanout 2 everywhere: f1 = f2 = 1, so every
+ *       inner node splits in two with its left part a multiple of l.  In
+ *       this file's interface a leaf size argument with ORC_TREE_FANOUT2
+ *       set selects that tree.
  *   R4  the hash tried at a node is mix64(lo + salt(level) + s) mod m.
  *   R5  rotation fitting puts a key in B iff (hi & 1) = 1; a rotation by r
  *       moves bit p of B's mask to bit (p + r) mod m.
@@ -60,6 +64,7 @@
 #define ORC_EBUCKET (-7)
 
 #define ORC_MAX_BUCKET 4096u
+#define ORC_TREE_FANOUT2 0x100u /* flag on a leaf size argument: fanout 2 everywhere */
 #define ORC_MAX_LEAF 24u
 #define ORC_MAX_PARTS 16u
 #define ORC_GOLDEN 0x9E3779B97F4A7C15ull
@@ -127,13 +132,18 @@ typedef struct {
     uint32_t lower2; /* largest lower-2 node: f2*f1*l        */
 } orc_shape;
 
-static orc_shape shape_of(uint32_t leaf) {
+static orc_shape shape_of(uint32_t leaf_arg) {
     orc_shape sh;
+    uint32_t leaf = leaf_arg & 0xFFu;
     sh.leaf = leaf;
-    sh.f1 = (35 * leaf + 55 + 99) / 100; /* ceil(0.35 l + 0.55) */
-    if (sh.f1 < 2) sh.f1 = 2;
-    sh.f2 = (21 * leaf + 90 + 99) / 100; /* ceil(0.21 l + 0.90) */
-    if (sh.f2 < 2) sh.f2 = 2;
+    if (leaf_arg & ORC_TREE_FANOUT2) {
+        sh.f1 = sh.f2 = 1;
+    } else {
+        sh.f1 = (35 * leaf + 55 + 99) / 100; /* ceil(0.35 l + 0.55) */
+        if (sh.f1 < 2) sh.f1 = 2;
+        sh.f2 = (21 * leaf + 90 + 99) / 100; /* ceil(0.21 l + 0.90) */
+        if (sh.f2 < 2) sh.f2 = 2;
+    }
     sh.lower1 = sh.f1 * leaf;
     sh.lower2 = sh.f2 * sh.lower1;
     return sh;
@@ -944,6 +954,8 @@ static int check_params(uint64_t n, uint32_t key_bytes, uint32_t leaf, uint32_t 
                         int bij) {
     if (bij < ORC_BIJ_PLAIN || bij > ORC_BIJ_SHOCKHASH) return ORC_EINVAL;
     if (key_bytes != 8 && key_bytes != 16) return ORC_EINVAL;
+    if (leaf & ~(ORC_TREE_FANOUT2 | 0xFFu)) return ORC_EINVAL;
+    leaf &= 0xFFu;
     if (leaf < 2 || leaf > ORC_MAX_LEAF) return ORC_EINVAL;
     if (bucket_size < 1 || bucket_size > 3000) return ORC_EINVAL;
     if (n >= (1ull << 32)) return ORC_EINVAL;

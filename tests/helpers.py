@@ -36,11 +36,12 @@ def golden_hex(name: str) -> list[int]:
 class NaiveChecker:
     """Walks each bucket's tree from the stored values and checks every node."""
 
-    def __init__(self, O, leaf: int, rotation: bool):
+    def __init__(self, O, leaf: int, rotation: bool, tree: int = 0):
         self.O = O
         self.leaf = leaf
         self.rotation = rotation
-        f1, f2 = O.fanouts(leaf)
+        self.tree = tree
+        f1, f2 = O.fanouts(leaf, tree)
         self.lower1 = f1 * leaf
         self.lower2 = f2 * f1 * leaf
         self.salts = {}
@@ -105,7 +106,7 @@ class NaiveChecker:
                 for y in range(x):
                     assert not self.leaf_ok(lo, hi, m, y), f"smaller leaf value {y} < {x} works"
             return 1
-        parts = self.O.parts(self.leaf, m)
+        parts = self.O.parts(self.leaf, m, self.tree)
         assert self.split_ok(lo, m, depth, x, parts), "stored split does not split"
         if x <= max_brute:
             for y in range(x):
