@@ -134,13 +134,14 @@ def cpu_baseline(w, keys, budget_s: float) -> dict:
     # size the sample from one bucket's single-thread time
     probe = W.sample_buckets(nb, 1, w.seed + 99)
     t0 = time.perf_counter()
-    O.build_sample(keys, w.leaf, w.bucket, w.rotation, probe, threads=1)
+    O.build_sample(keys, w.leaf, w.bucket, w.rotation, probe, threads=1, tree=w.tree)
     one = time.perf_counter() - t0
     count = int(max(1, min(nb, round(budget_s * cores / max(one, 1e-3)))))
     count = min(nb, max(cores, count - count % cores))  # at least one bucket per core
     sample = W.sample_buckets(nb, count, w.seed + 100)
     t0 = time.perf_counter()
-    vals, counts, st = O.build_sample(keys, w.leaf, w.bucket, w.rotation, sample, threads=cores)
+    vals, counts, st = O.build_sample(keys, w.leaf, w.bucket, w.rotation, sample, threads=cores,
+                                      tree=w.tree)
     dt = time.perf_counter() - t0
     hi, _ = O.fingerprint(keys)
     sample_keys = int(np.isin(bucket_index(hi, nb), sample.astype(np.int64)).sum())
@@ -261,6 +262,7 @@ def run_reference(args):
            "data": "synthetic", "impl": "reference",
            "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "bucket": w.bucket,
                       "rotation": int(w.rotation) == 1, "leaves": LEAF_NAMES[int(w.rotation)],
+                      "tree": "fanout 2" if w.tree else "lower aggregation levels",
                       "key_bytes": w.key_bytes, "sample": r["sample"]},
            "cpu_baseline": {"value": v, "unit": "keys/s", "cores": r["cores"], "kind": "oracle",
                             "sample": r["sample"]},
@@ -307,7 +309,8 @@ def weak_scaling_value(world: int, steps: int, n: int, total_ms: float) -> float
 def workload(args):
     w = W.WORKLOADS[args.workload]
     if args.n:
-        w = W.Workload(w.name + f"_n{args.n}", args.n, w.leaf, w.bucket, w.key_bytes, w.rotation, w.seed)
+        w = W.Workload(w.name + f"_n{args.n}", args.n, w.leaf, w.bucket, w.key_bytes, w.rotation,
+                       w.seed, w.tree)
     return w
 
 
@@ -334,7 +337,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for i in range(args.warmup):
-        M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation).close()
+        M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation, tree=w.tree).close()
     sampler = ClockSampler(local)
     sampler.start()
     step_ms, search_ms, evals, trials = [], [], 0, 0
@@ -345,7 +348,7 @@ def run_ours(args):
         flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (outside the step's events)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        g = M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation)
+        g = M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation, tree=w.tree)
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
@@ -375,7 +378,7 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            g = M.MPHF.build_host(host_view, w.leaf, w.bucket, w.rotation)
+            g = M.MPHF.build_host(host_view, w.leaf, w.bucket, w.rotation, tree=w.tree)
             blob = g.serialize()
             times.append(time.perf_counter() - t0)
             d2h = len(blob)
@@ -402,6 +405,7 @@ def run_ours(args):
            "data": "synthetic",
            "config": {"workload": w.name, "n": w.n, "leaf": w.leaf, "bucket": w.bucket,
                       "rotation": int(w.rotation) == 1, "leaves": LEAF_NAMES[int(w.rotation)],
+                      "tree": "fanout 2" if w.tree else "lower aggregation levels",
                       "key_bytes": w.key_bytes,
                       "l2": "flushed between steps (256 MB write)",
                       "parallelism": f"{world} independent builds (one per GPU)"},

@@ -78,6 +78,11 @@ typedef struct {
  *   threads_per_block, blocks_per_sm
  *                    launch shape of the search kernel; 0 = the tuned or
  *                    default choice.
+ *   tree_shape       MPHF_TREE_RECSPLIT: leaves under two lower aggregation
+ *                    levels with fanouts f1, f2 of l, fanout 2 above (Section
+ *                    2.2, "Splitting Trees"); MPHF_TREE_FANOUT2: fanout 2 for
+ *                    the entire tree, each left part a multiple of l (the
+ *                    configuration Appendix C uses with ShockHash leaves).
  *   leaf_method      how plain and rotation leaves are searched (same result
  *                    every time; ShockHash leaves have one search):
  *                    MPHF_LEAF_LOCKSTEP  every trial hashes all m keys
@@ -86,6 +91,8 @@ typedef struct {
  *                    MPHF_LEAF_TABLE     as EARLY, the rotation from a table of
  *                                        canonical rotations (leaves of <= 16
  *                                        keys; Section 4, "Lookup Tables"). */
+#define MPHF_TREE_RECSPLIT 0u
+#define MPHF_TREE_FANOUT2 1u
 #define MPHF_BIJECTION_PLAIN 0u
 #define MPHF_BIJECTION_ROTATION 1u
 #define MPHF_BIJECTION_SHOCKHASH 2u
@@ -106,7 +113,7 @@ typedef struct {
     uint32_t threads_per_block;
     uint32_t blocks_per_sm;
     uint32_t leaf_method;
-    uint32_t reserved;
+    uint32_t tree_shape;
 } mphf_build_params;
 
 /* Sizes and parameters of a built function. */
@@ -120,7 +127,7 @@ typedef struct {
     uint32_t ef_low_bits[2];   /* L of the key-count / bit-position sequences      */
     uint64_t ef_seq_words[4];  /* low, high words of sequence 0, then sequence 1   */
     uint32_t max_bucket;       /* largest bucket seen                              */
-    uint32_t reserved;
+    uint32_t tree_shape;       /* MPHF_TREE_*                                      */
 } mphf_info;
 
 /* Work done by the searches, per node kind (0 leaf, 1 lower-1 split, 2 lower-2
@@ -205,9 +212,13 @@ int mphf_get_stats(const mphf_t *h, mphf_stats *stats);
 /* Golomb-Rice parameter per node size m in [0, max_m] as the library uses it
  * (Section 2.2, "Representation": one parameter per tree layer, precomputed).
  * Writes max_m + 1 bytes to host memory. */
-int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t max_m, uint8_t *h_out);
+int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t tree_shape, uint32_t max_m,
+                   uint8_t *h_out);
 
-/* Copies the function to host memory: a header then the Golomb-Rice and
+/* Copies the function to host memory: a header of 16 64-bit words (magic,
+ * n, nb, leaf_size | tree_shape << 16, bucket_size, key_bytes,
+ * leaf_bijection, gr_bits, gr_words, ef_words, the two Elias-Fano low-bit
+ * counts, the four Elias-Fano sequence word counts) then the Golomb-Rice and
  * Elias-Fano words.  With h_buf NULL, *len receives the size needed. */
 int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream);
 
@@ -232,6 +243,8 @@ typedef struct {
     uint32_t key_bytes;
     uint32_t leaf_bijection;  /* MPHF_BIJECTION_* */
     uint64_t max_value;       /* 0 = MPHF_DEFAULT_MAX_VALUE */
+    uint32_t tree_shape;      /* MPHF_TREE_* */
+    uint32_t reserved;        /* 0 */
 } mphf_build_desc;
 
 int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream, mphf_t **outs,

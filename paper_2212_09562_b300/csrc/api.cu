@@ -39,17 +39,17 @@ struct DevTables {
 };
 
 // Per-device copies of the per-size tables; live until the process exits.
-int device_tables(int dev, uint32_t leaf, uint32_t bij, DevTables *out) {
+int device_tables(int dev, uint32_t leaf, uint32_t bij, uint32_t tree, DevTables *out) {
     static std::mutex mu;
     static std::map<uint64_t, DevTables> cache;
     std::lock_guard<std::mutex> g(mu);
-    uint64_t key = ((uint64_t)dev << 32) | (leaf << 2) | bij;
+    uint64_t key = ((uint64_t)dev << 32) | (tree << 16) | (leaf << 2) | bij;
     auto it = cache.find(key);
     if (it != cache.end()) {
         *out = it->second;
         return MPHF_OK;
     }
-    const SizeTables &t = size_tables(leaf, bij);
+    const SizeTables &t = size_tables(leaf, bij, tree);
     DevTables d;
     if (cudaMalloc(&d.tau, sizeof(t.tau)) != cudaSuccess) return MPHF_ENOMEM;
     if (cudaMalloc(&d.nodes, sizeof(t.nodes)) != cudaSuccess) return MPHF_ENOMEM;
@@ -207,11 +207,12 @@ const char *mphf_strerror(int code) {
     }
 }
 
-int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t max_m, uint8_t *h_out) {
+int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t tree_shape, uint32_t max_m,
+                   uint8_t *h_out) {
     if (!h_out || leaf_size < 2 || leaf_size > MPHF_MAX_LEAF || max_m > MPHF_MAX_BUCKET ||
-        leaf_bijection > MPHF_BIJECTION_SHOCKHASH)
+        leaf_bijection > MPHF_BIJECTION_SHOCKHASH || tree_shape > MPHF_TREE_FANOUT2)
         return MPHF_EINVAL;
-    const SizeTables &t = size_tables(leaf_size, leaf_bijection);
+    const SizeTables &t = size_tables(leaf_size, leaf_bijection, tree_shape);
     memcpy(h_out, t.tau, max_m + 1);
     return MPHF_OK;
 }
@@ -250,7 +251,8 @@ int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
     if (p->threads_per_block &&
         (p->threads_per_block % 32 || p->threads_per_block > 512 || p->threads_per_block < 64))
         return MPHF_EINVAL;
-    if (p->leaf_method > MPHF_LEAF_TABLE || p->leaf_bijection > MPHF_BIJECTION_SHOCKHASH)
+    if (p->leaf_method > MPHF_LEAF_TABLE || p->leaf_bijection > MPHF_BIJECTION_SHOCKHASH ||
+        p->tree_shape > MPHF_TREE_FANOUT2)
         return MPHF_EINVAL;
     return MPHF_OK;
 }
@@ -406,6 +408,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         d.max_value = j.maxv;
         d.leaf = j.p.leaf_size;
         d.bij = j.p.leaf_bijection;
+        d.tree = j.p.tree_shape;
         d.nb = (uint32_t)j.nb;
         d.k30 = 1u << 2;
         d.k27 = 1u << 5;
@@ -510,7 +513,8 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         launch_ef_write(h->bit_pos, j.nb + 1, e1.L, lo1, hi1, st);
         launch_rank_dir(hi0, e0.high_words, h->ef_dir, scan_tmp, st);
         launch_rank_dir(hi1, e1.high_words, h->ef_dir + h->ef_dir_len[0], scan_tmp, st);
-        launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.leaf_bijection, j.counters, st);
+        launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.leaf_bijection,
+                     j.p.tree_shape, j.counters, st);
         CU(cudaGetLastError());
     }
     cudaEventRecord(ev[4], st);
@@ -582,7 +586,9 @@ void start_job(Job &j, const void *d_keys, uint64_t n, const mphf_build_params &
     h->info.bucket_size = p.bucket_size;
     h->info.key_bytes = p.key_bytes;
     h->info.leaf_bijection = p.leaf_bijection;
-    int rc = device_tables(h->device, p.leaf_size, h->info.leaf_bijection, &h->tabs);
+    h->info.tree_shape = p.tree_shape;
+    int rc = device_tables(h->device, p.leaf_size, h->info.leaf_bijection, h->info.tree_shape,
+                           &h->tabs);
     if (rc) {
         release(h);
         j.h = nullptr;
@@ -656,7 +662,7 @@ static QueryView view_of(const mphf_t *h) {
     q.leaf = I.leaf_size;
     q.bij = I.leaf_bijection;
     q.key_bytes = I.key_bytes;
-    q.pad = 0;
+    q.tree = I.tree_shape;
     return q;
 }
 
@@ -746,7 +752,8 @@ int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream) {
         return MPHF_EINVAL;
     }
     uint64_t hd[16] = {0x3130485046504D52ull /* "RMPHF01" */, h->info.n, h->info.nb,
-                       h->info.leaf_size, h->info.bucket_size, h->info.key_bytes,
+                       h->info.leaf_size | ((uint64_t)h->info.tree_shape << 16),
+                       h->info.bucket_size, h->info.key_bytes,
                        h->info.leaf_bijection, h->info.gr_bits, h->info.gr_words,
                        h->info.ef_words, h->info.ef_low_bits[0], h->info.ef_low_bits[1],
                        h->info.ef_seq_words[0], h->info.ef_seq_words[1], h->info.ef_seq_words[2],
@@ -785,6 +792,7 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
         p.bucket_size = descs[i].bucket_size;
         p.key_bytes = descs[i].key_bytes;
         p.leaf_bijection = descs[i].leaf_bijection;
+        p.tree_shape = descs[i].tree_shape;
         p.max_value = descs[i].max_value ? descs[i].max_value : MPHF_DEFAULT_MAX_VALUE;
         outs[i] = nullptr;
         start_job(jobs[i], descs[i].d_keys, descs[i].n, p);
@@ -891,6 +899,7 @@ static void server_worker(mphf_server_t *S, int w) {
             p.bucket_size = d.bucket_size;
             p.key_bytes = d.key_bytes;
             p.leaf_bijection = d.leaf_bijection;
+            p.tree_shape = d.tree_shape;
             p.max_value = d.max_value ? d.max_value : MPHF_DEFAULT_MAX_VALUE;
             start_job(jobs[i], d.d_keys, d.n, p);
         }

@@ -1092,7 +1092,7 @@ template <int LEAF>
 __device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
                                BlockState &S) {
     const uint32_t tid = threadIdx.x, T = blockDim.x;
-    const Shape sh = make_shape(LEAF ? (uint32_t)LEAF : d.leaf);
+    const Shape sh = make_shape(LEAF ? (uint32_t)LEAF : d.leaf, d.tree);
     const uint64_t kbeg = d.bucket_off[bucket];
     const uint64_t M = d.bucket_off[bucket + 1] - kbeg;
     const uint64_t nbase = d.node_off[bucket];
@@ -1333,11 +1333,11 @@ __global__ void k_popcount(const uint64_t *words, uint64_t n, uint64_t *out) {
 
 // Stats: trials up to the stored value, and hash evaluations, per node kind.
 __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes,
-                        uint32_t leaf, uint32_t bij, unsigned long long *counters) {
+                        uint32_t leaf, uint32_t bij, uint32_t tree, unsigned long long *counters) {
     __shared__ unsigned long long acc[8];
     if (threadIdx.x < 8) acc[threadIdx.x] = 0;
     __syncthreads();
-    const Shape sh = make_shape(leaf);
+    const Shape sh = make_shape(leaf, tree);
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n_nodes;
          j += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t m = node_m[j];
@@ -1355,9 +1355,9 @@ __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t
 }
 
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
-                  uint32_t bij, uint64_t *counters, cudaStream_t st) {
+                  uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st) {
     if (n_nodes == 0) return;
-    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, leaf, bij,
+    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, leaf, bij, tree,
                                                           (unsigned long long *)counters);
     note_launches(1);
 }

@@ -9,6 +9,8 @@
 //   shape       leaves of l keys; lower aggregation fanouts
 //               f1 = max(2, ceil(0.35 l + 0.55)), f2 = max(2, ceil(0.21 l + 0.9));
 //               fanout 2 above, left part a multiple of the lower-2 size.
+//               The fanout-2 tree (Appendix C) has f1 = f2 = 1: every inner
+//               node splits in two, its left part a multiple of l.
 //   node hash   mix64(lo + salt(level) + s) mod m.
 #pragma once
 #include <stdint.h>
@@ -63,11 +65,13 @@ struct Shape {
     uint32_t lower2;  // f2 * f1 * l: largest node cut into lower-1 nodes
 };
 
-__host__ __device__ __forceinline__ Shape make_shape(uint32_t leaf) {
+// tree: 0 = the two lower aggregation levels, 1 = fanout 2 everywhere.
+__host__ __device__ __forceinline__ Shape make_shape(uint32_t leaf, uint32_t tree = 0) {
     uint32_t f1 = (35u * leaf + 154u) / 100u;  // ceil((35 l + 55) / 100)
     uint32_t f2 = (21u * leaf + 189u) / 100u;  // ceil((21 l + 90) / 100)
     f1 = f1 < 2 ? 2 : f1;
     f2 = f2 < 2 ? 2 : f2;
+    if (tree) f1 = f2 = 1;
     Shape s;
     s.leaf = leaf;
     s.lower1 = f1 * leaf;

@@ -21,6 +21,7 @@ struct InstDesc {
     uint32_t *status;            // ST_* bits
     uint64_t max_value;
     uint32_t leaf, bij;          // bij: MPHF_BIJECTION_* leaf method
+    uint32_t tree;               // MPHF_TREE_*: lower aggregation levels or fanout 2 everywhere
     uint32_t nb;
     uint32_t k30, k27, k31;      // 4, 32, 2: multipliers of the hash's xor-shifts
     uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
@@ -89,7 +90,7 @@ void launch_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low, u
 void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint64_t *tmp,
                      cudaStream_t st);
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
-                  uint32_t bij, uint64_t *counters, cudaStream_t st);
+                  uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st);
 
 // Query side.
 struct QueryView {
@@ -101,7 +102,7 @@ struct QueryView {
     const uint8_t *tau;
     const uint32_t *nodes_tab, *fixed_tab;
     uint64_t nb;
-    uint32_t leaf, bij, key_bytes, pad;
+    uint32_t leaf, bij, key_bytes, tree;
 };
 void launch_query(const QueryView &q, const void *keys, uint64_t n, uint64_t *out, cudaStream_t st);
 void launch_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad,

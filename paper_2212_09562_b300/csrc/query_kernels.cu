@@ -68,7 +68,7 @@ __device__ __forceinline__ uint64_t node_value(const uint64_t *gr, uint64_t fixe
 }
 
 __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out) {
-    const Shape sh = make_shape(q.leaf);
+    const Shape sh = make_shape(q.leaf, q.tree);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t *p = (const uint64_t *)keys;

@@ -137,9 +137,9 @@ uint8_t kiely(double p) {
 
 }  // namespace
 
-uint8_t node_tau(uint32_t leaf, uint32_t bij, uint32_t m) {
+uint8_t node_tau(uint32_t leaf, uint32_t bij, uint32_t tree, uint32_t m) {
     if (m < 2) return 0;
-    Shape s = make_shape(leaf);
+    Shape s = make_shape(leaf, tree);
     double p;
     if (m > leaf)
         p = split_success(s, m);
@@ -152,19 +152,20 @@ uint8_t node_tau(uint32_t leaf, uint32_t bij, uint32_t m) {
     return kiely(p);
 }
 
-const SizeTables &size_tables(uint32_t leaf, uint32_t bij) {
+const SizeTables &size_tables(uint32_t leaf, uint32_t bij, uint32_t tree) {
     static std::mutex mu;
     static std::map<uint32_t, std::unique_ptr<SizeTables>> cache;
     std::lock_guard<std::mutex> g(mu);
-    uint32_t key = leaf * 4 + bij;
+    uint32_t key = (leaf * 4 + bij) * 2 + (tree ? 1 : 0);
     auto it = cache.find(key);
     if (it != cache.end()) return *it->second;
     auto t = std::make_unique<SizeTables>();
     t->leaf = leaf;
     t->bij = bij;
-    Shape s = make_shape(leaf);
+    t->tree = tree ? 1 : 0;
+    Shape s = make_shape(leaf, t->tree);
     for (uint32_t m = 0; m <= 4096; m++) {
-        t->tau[m] = node_tau(leaf, bij, m);
+        t->tau[m] = node_tau(leaf, bij, t->tree, m);
         if (m < 2) {
             t->nodes[m] = 0;
             t->fixed[m] = 0;

@@ -33,6 +33,8 @@ DEFAULT_MAX_VALUE = (1 << 40) - 1
 LEAF_LOCKSTEP, LEAF_EARLY, LEAF_TABLE = 0, 1, 2
 # leaf bijection methods; every ``rotation`` argument takes a bool or one of these
 PLAIN, ROTATION, SHOCKHASH = 0, 1, 2
+# tree shapes: RecSplit's lower aggregation levels, or fanout 2 everywhere (Appendix C)
+TREE_RECSPLIT, TREE_FANOUT2 = 0, 1
 SH_SEED_BITS = 40  # a ShockHash leaf's value: seed below bit 40, retrieval vector above
 
 
@@ -63,7 +65,7 @@ class BuildParams(ctypes.Structure):
                 ("key_bytes", ctypes.c_uint32), ("leaf_bijection", ctypes.c_uint32),
                 ("max_value", ctypes.c_uint64), ("allocator", ctypes.c_void_p),
                 ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
-                ("leaf_method", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("leaf_method", ctypes.c_uint32), ("tree_shape", ctypes.c_uint32)]
 
 
 class Info(ctypes.Structure):
@@ -73,7 +75,7 @@ class Info(ctypes.Structure):
                 ("gr_bits", ctypes.c_uint64), ("gr_words", ctypes.c_uint64),
                 ("ef_words", ctypes.c_uint64), ("ef_low_bits", ctypes.c_uint32 * 2),
                 ("ef_seq_words", ctypes.c_uint64 * 4), ("max_bucket", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("tree_shape", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -95,7 +97,8 @@ class RequestTimes(ctypes.Structure):
 class BuildDesc(ctypes.Structure):
     _fields_ = [("d_keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
                 ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
-                ("leaf_bijection", ctypes.c_uint32), ("max_value", ctypes.c_uint64)]
+                ("leaf_bijection", ctypes.c_uint32), ("max_value", ctypes.c_uint64),
+                ("tree_shape", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 # Every entry point of include/mphf.h: name -> (restype, argtypes)
@@ -112,7 +115,7 @@ SIGNATURES = {
     "mphf_get_values": (_I, [_P, _P, _P, _P, _P]),
     "mphf_get_bits": (_I, [_P, _P, _P, _P, _P]),
     "mphf_get_stats": (_I, [_P, _P]),
-    "mphf_tau_table": (_I, [_U32, _U32, _U32, _P]),
+    "mphf_tau_table": (_I, [_U32, _U32, _U32, _U32, _P]),
     "mphf_serialize": (_I, [_P, _P, _P, _P]),
     "mphf_free": (_I, [_P]),
     "mphf_strerror": (ctypes.c_char_p, [_I]),
@@ -211,8 +214,9 @@ class MPHF:
     def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
               max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
               blocks_per_sm: int = 0, stream=None, tuned: bool = False,
-              leaf_method: int | None = None) -> "MPHF":
+              leaf_method: int | None = None, tree: int = TREE_RECSPLIT) -> "MPHF":
         """rotation: True/False or PLAIN, ROTATION, SHOCKHASH (the leaf method);
+        tree: TREE_RECSPLIT or TREE_FANOUT2;
         tuned=True takes the launch shape from the autotuner's cache;
         leaf_method: LEAF_LOCKSTEP (default), LEAF_EARLY or LEAF_TABLE."""
         n, kb = key_layout(keys)
@@ -222,6 +226,7 @@ class MPHF:
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
         p.leaf_bijection = bijection(rotation)
+        p.tree_shape = tree
         p.max_value = max_value
         p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
         if leaf_method is not None:
@@ -235,13 +240,14 @@ class MPHF:
     @classmethod
     def build_host(cls, keys: np.ndarray, leaf_size: int = 16, bucket_size: int = 2000,
                    rotation=True, max_value: int = DEFAULT_MAX_VALUE,
-                   stream=None) -> "MPHF":
+                   stream=None, tree: int = TREE_RECSPLIT) -> "MPHF":
         """Build from keys in host memory (copied to the device inside the call)."""
         keys = np.ascontiguousarray(keys)
         kb = 8 if keys.ndim == 1 else 16
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
         p.leaf_bijection = bijection(rotation)
+        p.tree_shape = tree
         p.max_value = max_value
         h = ctypes.c_void_p()
         rc = lib().mphf_build_host(keys.ctypes.data if len(keys) else None, len(keys),
@@ -337,22 +343,23 @@ def kernel_launches() -> int:
     return int(lib().mphf_kernel_launches())
 
 
-def tau_table(leaf_size: int, rotation, max_m: int = MAX_BUCKET) -> np.ndarray:
+def tau_table(leaf_size: int, rotation, max_m: int = MAX_BUCKET,
+              tree: int = TREE_RECSPLIT) -> np.ndarray:
     out = np.zeros(max_m + 1, np.uint8)
-    _check(lib().mphf_tau_table(leaf_size, bijection(rotation), max_m, out.ctypes.data),
+    _check(lib().mphf_tau_table(leaf_size, bijection(rotation), tree, max_m, out.ctypes.data),
            "mphf_tau_table")
     return out
 
 
 def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation=True,
-                max_value: int = 0, stream=None) -> list[MPHF]:
+                max_value: int = 0, stream=None, tree: int = TREE_RECSPLIT) -> list[MPHF]:
     """Many independent builds in one call (see mphf_build_batch)."""
     count = len(keys_list)
     descs = (BuildDesc * max(count, 1))()
     for i, (k, l) in enumerate(zip(keys_list, leaf_sizes)):
         n, kb = key_layout(k)
         descs[i] = BuildDesc(k.data_ptr() if n else None, n, l, bucket_size, kb,
-                             bijection(rotation), max_value)
+                             bijection(rotation), max_value, tree, 0)
     outs = (ctypes.c_void_p * max(count, 1))()
     sts = (ctypes.c_int * max(count, 1))()
     rc = lib().mphf_build_batch(descs, count, _stream(stream), outs, sts)
@@ -376,10 +383,10 @@ class Server:
         self._keep = {}  # ticket -> key tensor, alive until the request is polled
 
     def submit(self, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
-               max_value: int = 0) -> int:
+               max_value: int = 0, tree: int = TREE_RECSPLIT) -> int:
         n, kb = key_layout(keys)
         d = BuildDesc(keys.data_ptr() if n else None, n, leaf_size, bucket_size, kb,
-                      bijection(rotation), max_value)
+                      bijection(rotation), max_value, tree, 0)
         t = ctypes.c_uint64()
         _check(lib().mphf_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)),
                "mphf_server_submit")

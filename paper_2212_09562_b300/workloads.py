@@ -11,6 +11,8 @@ random 128-bit integers used directly, or random strings).  The workloads:
 * ``rot_l16``    n = 10,000,000 distinct uniform 64-bit keys, l = 16, b = 2000, rotation fitting
 * ``shock_l16``  the keys and shape of ``rot_l16`` (another seed) with ShockHash leaves
   (Appendix C)
+* ``shockf2_l24`` n = 10,000,000 distinct uniform 64-bit keys, l = 24, b = 2000, ShockHash
+  leaves under a fanout-2 tree (the configuration of Appendix C)
 * ``batch``      4,096 builds, n_i = floor(10^U(3,6)), l_i uniform in {8, 12, 16}, b = 2000
 * ``serve``      Poisson request stream, mean 200/s, n ~ floor(10^U(4,7)) 16-byte keys, l = 16
 """
@@ -32,6 +34,7 @@ class Workload:
     key_bytes: int
     rotation: int  # leaf method: 0 / False plain, 1 / True rotation fitting, 2 ShockHash
     seed: int
+    tree: int = 0  # 0 lower aggregation levels, 1 fanout 2 everywhere
 
 
 WORKLOADS = {
@@ -39,6 +42,7 @@ WORKLOADS = {
     "rot_l12": Workload("rot_l12", 1_000_000, 12, 1000, 16, True, SEED_BASE + 2),
     "rot_l16": Workload("rot_l16", 10_000_000, 16, 2000, 8, True, SEED_BASE + 3),
     "shock_l16": Workload("shock_l16", 10_000_000, 16, 2000, 8, 2, SEED_BASE + 4),
+    "shockf2_l24": Workload("shockf2_l24", 10_000_000, 24, 2000, 8, 2, SEED_BASE + 5, 1),
 }
 
 

@@ -63,8 +63,8 @@ def test_failing_member_does_not_disturb_the_others(torch):
     dkeys = [dev(torch, k) for k in keys]
     descs = (M.BuildDesc * 6)()
     for i, dk in enumerate(dkeys):
-        descs[i] = M.BuildDesc(dk.data_ptr(), dk.shape[0], 12, 200, 8, 1, 0)
-    descs[5] = M.BuildDesc(dkeys[0].data_ptr(), dkeys[0].shape[0], 1, 200, 8, 1, 0)  # bad leaf size
+        descs[i] = M.BuildDesc(dk.data_ptr(), dk.shape[0], 12, 200, 8, 1, 0, 0, 0)
+    descs[5] = M.BuildDesc(dkeys[0].data_ptr(), dkeys[0].shape[0], 1, 200, 8, 1, 0, 0, 0)  # bad leaf size
     import ctypes
     outs = (ctypes.c_void_p * 6)()
     sts = (ctypes.c_int * 6)()

@@ -96,7 +96,7 @@ def test_batch_mixes_leaf_methods(torch, orc):
     dkeys = [to_dev(torch, k) for k in keys]
     descs = (M.BuildDesc * len(specs))()
     for i, ((n, leaf, bij), dk) in enumerate(zip(specs, dkeys)):
-        descs[i] = M.BuildDesc(dk.data_ptr() if n else None, n, leaf, 500, 8, bij, 0)
+        descs[i] = M.BuildDesc(dk.data_ptr() if n else None, n, leaf, 500, 8, bij, 0, 0, 0)
     outs = (ctypes.c_void_p * len(specs))()
     sts = (ctypes.c_int * len(specs))()
     stream = torch.cuda.current_stream().cuda_stream

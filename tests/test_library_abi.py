@@ -57,18 +57,21 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     p = M.default_params()
     for field, value in [("leaf_size", 1), ("leaf_size", 25), ("bucket_size", 0),
                          ("bucket_size", 3001), ("key_bytes", 4), ("threads_per_block", 100),
-                         ("leaf_bijection", 3), ("leaf_method", 3)]:
+                         ("leaf_bijection", 3), ("leaf_method", 3), ("tree_shape", 2)]:
         q = M.default_params()
         setattr(q, field, value)
         assert lib.mphf_build_ex(None, 0, ctypes.byref(q), None, ctypes.byref(h)) == M.EINVAL
     assert lib.mphf_build_ex(None, 5, ctypes.byref(p), None, ctypes.byref(h)) == M.EINVAL
     assert lib.mphf_query(None, None, 0, None, None) == M.EINVAL
-    assert lib.mphf_tau_table(1, 1, 10, None) == M.EINVAL
+    assert lib.mphf_tau_table(1, 1, 0, 10, None) == M.EINVAL
     out = np.zeros(11, np.uint8)
-    assert lib.mphf_tau_table(8, 3, 10, out.ctypes.data) == M.EINVAL
+    assert lib.mphf_tau_table(8, 3, 0, 10, out.ctypes.data) == M.EINVAL
+    assert lib.mphf_tau_table(8, 1, 2, 10, out.ctypes.data) == M.EINVAL
 
 
 @pytest.mark.parametrize("leaf", [2, 3, 5, 7, 8, 10, 12, 16, 20, 24])
 @pytest.mark.parametrize("rotation", [M.PLAIN, M.ROTATION, M.SHOCKHASH])
-def test_tau_tables_equal_the_oracle(lib, orc, leaf, rotation):
-    assert np.array_equal(M.tau_table(leaf, rotation), orc.tau_table(leaf, rotation))
+@pytest.mark.parametrize("tree", [M.TREE_RECSPLIT, M.TREE_FANOUT2])
+def test_tau_tables_equal_the_oracle(lib, orc, leaf, rotation, tree):
+    assert np.array_equal(M.tau_table(leaf, rotation, tree=tree),
+                          orc.tau_table(leaf, rotation, tree=tree))
