@@ -378,6 +378,9 @@ struct DivRT {
 #ifndef MPHF_RTC
 #define MPHF_RTC 1
 #endif
+#ifndef MPHF_RED_MODE
+#define MPHF_RED_MODE 1
+#endif
 
 __device__ __forceinline__ void xorshift_mul(uint32_t &zl, uint32_t &zh, uint32_t k) {
     uint32_t a, b, c;
@@ -455,6 +458,20 @@ __device__ __forceinline__ uint32_t mod_halves(const ModCTR<MM> &r, uint32_t hl,
         constexpr uint32_t c = (uint32_t)((1ull << 32) % MM);
 #endif
         uint64_t t = (uint64_t)hh * c + hl;
+#if MPHF_RED_MODE == 1
+        // c = 2^k for every full node size of the benchmarks (32 at 112, 256
+        // at 560, 16 at 60 and 240, 64 at 96): fold t = th 2^32 + tl as
+        // tl + th 2^k on the ALU, with the carry folded once more
+        constexpr uint32_t cc = (uint32_t)((1ull << 32) % MM);
+        if constexpr ((cc & (cc - 1)) == 0) {
+            constexpr uint32_t k = bit_width_ce(cc) - 1;
+            const uint32_t th = (uint32_t)(t >> 32), tl = (uint32_t)t;
+            const uint32_t add = th << k;
+            const uint32_t ul = tl + add;
+            const uint32_t v = ul + (ul < add ? cc : 0u);  // carry out of 2^32 is worth c
+            return v % MM;
+        }
+#endif
         uint64_t u = (uint64_t)(uint32_t)(t >> 32) * c + (uint32_t)t;
         uint32_t v = (uint32_t)(u >> 32) * c + (uint32_t)u;
         return v % MM;
@@ -738,17 +755,15 @@ __device__ __forceinline__ uint64_t leaf_cyclic(const uint64_t *xs, const uint8_
 }
 
 // Any two equal lo words among keys [0, m) of the block's bucket.
-// ShockHash leaf (Appendix C), one warp per leaf and one seed per round.
-// Lane i < m hashes key i to its two cells c0 = lo32(h) mod m and
-// c1 = hi32(h) mod m.  The keys are the edges of a multigraph on the m
-// cells; a bijection choosing one cell per key exists iff no component gets
-// more keys than cells.  Lane c holds the cell mask of cell c's component and
-// `cyc` the cells of components that already hold their one cycle, so every
-// edge is a few warp-uniform shuffles and the round stops at the first
-// component that would get a second cycle.  An accepted graph gets its
-// canonical bits (leaf_shock_bits) and its retrieval vector
-// (leaf_shock_solve); the smallest seed with both is stored with the vector
-// in bits MPHF_SH_BITS and up.
+// ShockHash leaf (Appendix C), one warp per leaf, one seed per lane and
+// round.  Under seed s key i has the cells c0 = lo32(h) mod m and
+// c1 = hi32(h) mod m; the keys are the edges of a multigraph on the m cells,
+// and a bijection choosing one cell per key exists iff no component gets
+// more keys than cells.  Each lane runs its own union-find over the edges
+// (shock_trial); the smallest accepted seeds of the round then get their
+// canonical bits (leaf_shock_bits) and retrieval vector (leaf_shock_solve)
+// from the whole warp, and the first with a solvable system is stored, with
+// the vector in bits MPHF_SH_BITS and up.
 __device__ __forceinline__ uint32_t leaf_shock_bits(uint32_t c0, uint32_t c1, uint64_t lo, uint32_t m,
                                                     uint32_t lane) {
     const bool key = lane < m;
@@ -834,19 +849,49 @@ __device__ __forceinline__ bool leaf_shock_solve(uint32_t row, uint32_t rhs, uin
     return true;
 }
 
+// Component labels of up to 24 cells, one byte per cell in NW <= 6
+// registers (cell c in byte c & 3 of w[c >> 2]); a component's label is one
+// of its cells.  Relabelling compares all bytes at once.
+template <int NW>
+struct CellLabels {
+    uint32_t w[NW];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < NW; i++) w[i] = 0x03020100u + 0x04040404u * (uint32_t)i;
+    }
+    __device__ __forceinline__ uint32_t get(uint32_t c) const {
+        const uint32_t r = c >> 2;
+        uint32_t x = w[0];
+#pragma unroll
+        for (int i = 1; i < NW; i++) x = r == (uint32_t)i ? w[i] : x;
+        return (x >> ((c & 3) * 8)) & 0xFFu;
+    }
+    // every byte equal to `from` becomes `to`
+    __device__ __forceinline__ void relabel(uint32_t from, uint32_t to) {
+        const uint32_t bf = from * 0x01010101u, diff = bf ^ (to * 0x01010101u);
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+            const uint32_t t = w[i] ^ bf;  // zero bytes where the label is `from`
+            const uint32_t nonzero = ((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t;
+            const uint32_t zero_hi = ~nonzero & 0x80808080u;
+            w[i] ^= ((zero_hi >> 7) * 0xFFu) & diff;
+        }
+    }
+};
+
+// One lane's trial: true iff the cells of the m keys under seed s admit a
+// bijection.  `cyc` marks the labels of components that hold their cycle.
 template <uint32_t MT>
-__device__ __forceinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *los, uint32_t m_rt,
-                                               const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
+__device__ __forceinline__ bool shock_trial(const uint64_t *xs, uint32_t m_rt, uint64_t s,
+                                            const Mixer &mx, const ModRT &mod) {
     const uint32_t m = MT ? MT : m_rt;
-    const bool key = lane < m;
-    const uint64_t x = key ? xs[lane] : 0;   // lo + salt(0)
-    const uint64_t lo = key ? los[lane] : 0;
-    const uint64_t row_salt = level_salt(MPHF_SH_ROW_LEVEL);
-    const ModRT mod = make_mod(m);
-    if (maxv > MPHF_SH_MASK) maxv = MPHF_SH_MASK;
-    for (uint64_t s = 0;; s++) {
+    constexpr int NW = MT ? (int)((MT + 3) / 4) : 6;
+    CellLabels<NW> L;
+    L.init();
+    uint32_t cyc = 0;
+    for (uint32_t i = 0; i < m; i++) {
         uint32_t hl, hh;
-        mx(x + s, hl, hh);
+        mx(xs[i] + s, hl, hh);
         uint32_t c0, c1;
         if constexpr (MT != 0) {
             c0 = hl % MT;
@@ -855,36 +900,49 @@ __device__ __forceinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_
             c0 = mod32(mod, hl);
             c1 = mod32(mod, hh);
         }
-        uint32_t cm = 1u << lane, cyc = 0;
-        bool ok = true;
-        for (uint32_t i = 0; i < m; i++) {
-            const uint32_t u = __shfl_sync(0xffffffffu, c0, i), v = __shfl_sync(0xffffffffu, c1, i);
-            const uint32_t mu = __shfl_sync(0xffffffffu, cm, u);
-            if ((mu >> v) & 1) {  // both cells in one component: it closes its cycle
-                if (cyc & mu) {
-                    ok = false;
-                    break;
-                }
-                cyc |= mu;
-            } else {
-                const uint32_t mv = __shfl_sync(0xffffffffu, cm, v);
-                if ((cyc & mu) && (cyc & mv)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t mm = mu | mv;
-                if (cyc & mm) cyc |= mm;
-                if ((mm >> lane) & 1) cm = mm;
-            }
+        const uint32_t a = L.get(c0), b = L.get(c1);
+        if (a == b) {  // closes the component's cycle
+            if ((cyc >> a) & 1) return false;
+            cyc |= 1u << a;
+        } else {
+            const uint32_t ca = (cyc >> a) & 1, cb = (cyc >> b) & 1;
+            if (ca & cb) return false;
+            L.relabel(b, a);
+            cyc |= cb << a;
         }
-        if (ok) {
+    }
+    return true;
+}
+
+// Not inlined: its label registers would otherwise push the split searches
+// of the same kernel past the 64-register budget.
+template <uint32_t MT>
+__device__ __noinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *los, uint32_t m_rt,
+                                               const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
+    const uint32_t m = MT ? MT : m_rt;
+    const bool key = lane < m;
+    const uint64_t x = key ? xs[lane] : 0;  // lo + salt(0)
+    const uint64_t lo = key ? los[lane] : 0;
+    const uint64_t row_salt = level_salt(MPHF_SH_ROW_LEVEL);
+    const ModRT mod = make_mod(m);
+    if (maxv > MPHF_SH_MASK) maxv = MPHF_SH_MASK;
+    for (uint64_t s0 = 0;; s0 += 32) {
+        const uint64_t mine = s0 + lane;
+        const bool ok = mine <= maxv && shock_trial<MT>(xs, m, mine, mx, mod);
+        uint32_t ball = __ballot_sync(0xffffffffu, ok);
+        while (ball) {  // accepted seeds, smallest first
+            const uint64_t s = s0 + (uint32_t)(__ffs(ball) - 1);
+            ball &= ball - 1;
+            uint32_t hl, hh;
+            mx(x + s, hl, hh);
+            const uint32_t c0 = key ? mod32(mod, hl) : 0u, c1 = key ? mod32(mod, hh) : 0u;
             const uint32_t beta = leaf_shock_bits(c0, c1, lo, m, lane);
             const uint64_t r = mix64(lo + row_salt + s);
             const uint32_t row = key ? ((uint32_t)r & ((1u << m) - 1)) : 0u;
             uint32_t z;
             if (leaf_shock_solve(row, key ? beta : 0u, m, lane, z)) return s | ((uint64_t)z << MPHF_SH_BITS);
         }
-        if (s >= maxv) {
+        if (s0 + 32 > maxv) {
             limit = true;
             return 0;
         }
