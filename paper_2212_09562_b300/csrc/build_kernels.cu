@@ -555,27 +555,30 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
     }
 }
 
-// Fanout-2 split: one counter of keys hashed below `left`.
+// Fanout-2 split: the number of keys hashed below `left` must be `left`.
+// One seed per warp and round, the lanes sharing the node's keys, so a round
+// tests 16 seeds (512 threads): a fanout-2 split of m keys needs about
+// sqrt(pi m / 2) trials, far fewer than one seed per thread would test.
 template <class Mod>
 __device__ __forceinline__ uint64_t search_upper(const uint64_t *xs, uint32_t m, Mod mod, uint32_t left,
                                  const Mixer &mx, uint64_t maxv, bool &limit, BlockState &S) {
-    const uint32_t T = blockDim.x;
-    for (uint64_t base = 0;; base += T) {
-        uint64_t s = base + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31, W = blockDim.x >> 5;
+    for (uint64_t base = 0;; base += W) {
+        const uint64_t s = base + (threadIdx.x >> 5);
         uint32_t cnt = 0;
-#pragma unroll 4
-        for (uint32_t i = 0; i < m; i++) {
+        for (uint32_t i = lane; i < m; i += 32) {
             uint32_t hl, hh;
             mx(xs[i] + s, hl, hh);
             cnt += mod_halves(mod, hl, hh) < left;
         }
-        bool ok = cnt == left && s <= maxv;
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        const bool ok = cnt == left && s <= maxv;  // the same in every lane of the warp
         if (__syncthreads_or(ok)) {
-            if (ok) atomicMin(&S.found, (unsigned long long)s);
+            if (ok && lane == 0) atomicMin(&S.found, (unsigned long long)s);
             __syncthreads();
             return S.found;
         }
-        if (base + T > maxv) {
+        if (base + W > maxv) {
             limit = true;
             return 0;
         }
