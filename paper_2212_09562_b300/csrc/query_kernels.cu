@@ -41,10 +41,11 @@ __device__ __forceinline__ uint64_t select_from(const uint64_t *w, uint64_t star
 }
 
 // Element i of an Elias-Fano sequence, select on the high bits through the
-// rank directory dir (ones before each word).
+// rank directory dir (ones before each word).  With `next` it also returns
+// element i + 1, whose high-bit one is the next one after element i's.
 __device__ __forceinline__ uint64_t ef_get(const uint64_t *low, const uint64_t *high,
                                            const uint64_t *dir, uint64_t nwords, uint32_t L,
-                                           uint64_t i) {
+                                           uint64_t i, uint64_t *next = nullptr) {
     uint64_t a = 0, b = nwords - 1;
     while (a < b) {
         uint64_t mid = (a + b + 1) >> 1;
@@ -55,16 +56,36 @@ __device__ __forceinline__ uint64_t ef_get(const uint64_t *low, const uint64_t *
     }
     uint64_t word = high[a];
     for (uint64_t r = i - dir[a]; r; r--) word &= word - 1;
-    uint64_t sel = a * 64 + (uint64_t)(__ffsll((long long)word) - 1);
+    const uint64_t sel = a * 64 + (uint64_t)(__ffsll((long long)word) - 1);
+    if (next) {
+        word &= word - 1;  // the ones after element i's, in this word and then the next ones
+        uint64_t wi = a;
+        while (!word) word = high[++wi];
+        const uint64_t sel1 = wi * 64 + (uint64_t)(__ffsll((long long)word) - 1);
+        *next = ((sel1 - i - 1) << L) | read_bits(low, (i + 1) * L, L);
+    }
     return ((sel - i) << L) | read_bits(low, i * L, L);
 }
 
+// Unary parts of one bucket, read front to back: the walk visits nodes in
+// increasing preorder index, so one cursor serves every level.  `pos` is the
+// first bit of code `count` (after `count` ones from the region's start).
+struct UnaryCursor {
+    uint64_t pos, count;
+    // the unary value (zeros before the one) of code idx >= count
+    __device__ __forceinline__ uint64_t value(const uint64_t *gr, uint64_t idx) {
+        const uint64_t begin = idx == count ? pos : select_from(gr, pos, idx - count - 1) + 1;
+        const uint64_t end = select_from(gr, begin, 0);
+        pos = end + 1;
+        count = idx + 1;
+        return end - begin;
+    }
+};
+
 __device__ __forceinline__ uint64_t node_value(const uint64_t *gr, uint64_t fixed_pos, uint32_t tau,
-                                               uint64_t ustart, uint64_t idx) {
-    uint64_t fixed = read_bits(gr, fixed_pos, tau);
-    uint64_t end = select_from(gr, ustart, idx);
-    uint64_t begin = idx == 0 ? ustart : select_from(gr, ustart, idx - 1) + 1;
-    return ((end - begin) << tau) | fixed;
+                                               UnaryCursor &u, uint64_t idx) {
+    const uint64_t fixed = read_bits(gr, fixed_pos, tau);
+    return (u.value(gr, idx) << tau) | fixed;
 }
 
 __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out) {
@@ -77,20 +98,22 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
         uint64_t hi, lo;
         fingerprint(w0, w1, hi, lo);
         uint64_t b = mulhi64(hi, q.nb);
-        uint64_t cum = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_high_words[0], q.ef_L[0], b);
-        uint64_t nxt = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_high_words[0], q.ef_L[0], b + 1);
-        uint64_t start = ef_get(q.ef_low[1], q.ef_high[1], q.ef_dir[1], q.ef_high_words[1], q.ef_L[1], b);
+        uint64_t nxt;
+        const uint64_t cum = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_high_words[0],
+                                    q.ef_L[0], b, &nxt);
+        const uint64_t start = ef_get(q.ef_low[1], q.ef_high[1], q.ef_dir[1], q.ef_high_words[1],
+                                      q.ef_L[1], b);
         uint32_t m = (uint32_t)(nxt - cum);
         if (m > 4096) {  // not a key of the built set (or a corrupt function)
             out[i] = cum;
             continue;
         }
-        const uint64_t ustart = start + q.fixed_tab[m];
+        UnaryCursor ucur{start + q.fixed_tab[m], 0};
         uint64_t fpos = start, idx = 0, rank = 0;
         uint32_t depth = 0;
         while (m > sh.leaf) {
             uint32_t t = q.tau[m];
-            uint64_t x = node_value(q.gr, fpos, t, ustart, idx);
+            uint64_t x = node_value(q.gr, fpos, t, ucur, idx);
             uint32_t pos = make_mod(m)(mix64(lo + level_salt(salt_level(sh, m, depth)) + x));
             uint32_t c;
             if (m > sh.lower2)
@@ -112,7 +135,7 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
             out[i] = cum + rank;
             continue;
         }
-        uint64_t x = node_value(q.gr, fpos, q.tau[m], ustart, idx);
+        uint64_t x = node_value(q.gr, fpos, q.tau[m], ucur, idx);
         const ModRT mod = make_mod(m);
         uint64_t pos;
         if (q.bij == MPHF_BIJECTION_PLAIN) {
