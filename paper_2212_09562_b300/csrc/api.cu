@@ -36,7 +36,34 @@ struct DevTables {
     uint8_t *tau = nullptr;
     uint32_t *nodes = nullptr;
     uint32_t *fixed = nullptr;
+    uint16_t *left = nullptr;
+    uint32_t *mod_c = nullptr;
+    uint64_t *mod_M = nullptr;
 };
+
+// Per-device copy of the exact-remainder constants per node size.
+int device_mod_tables(int dev, uint32_t **c, uint64_t **M) {
+    static std::mutex mu;
+    static std::map<int, std::pair<uint32_t *, uint64_t *>> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(dev);
+    if (it == cache.end()) {
+        const ModTables &t = mod_tables();
+        uint32_t *dc = nullptr;
+        uint64_t *dM = nullptr;
+        if (cudaMalloc(&dc, sizeof(t.c)) != cudaSuccess || cudaMalloc(&dM, sizeof(t.M)) != cudaSuccess) {
+            cudaGetLastError();
+            return MPHF_ENOMEM;
+        }
+        if (cudaMemcpy(dc, t.c, sizeof(t.c), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dM, t.M, sizeof(t.M), cudaMemcpyHostToDevice) != cudaSuccess)
+            return MPHF_ECUDA;
+        it = cache.emplace(dev, std::make_pair(dc, dM)).first;
+    }
+    *c = it->second.first;
+    *M = it->second.second;
+    return MPHF_OK;
+}
 
 // Per-device copies of the per-size tables; live until the process exits.
 int device_tables(int dev, uint32_t leaf, uint32_t bij, uint32_t tree, DevTables *out) {
@@ -54,10 +81,14 @@ int device_tables(int dev, uint32_t leaf, uint32_t bij, uint32_t tree, DevTables
     if (cudaMalloc(&d.tau, sizeof(t.tau)) != cudaSuccess) return MPHF_ENOMEM;
     if (cudaMalloc(&d.nodes, sizeof(t.nodes)) != cudaSuccess) return MPHF_ENOMEM;
     if (cudaMalloc(&d.fixed, sizeof(t.fixed)) != cudaSuccess) return MPHF_ENOMEM;
+    if (cudaMalloc(&d.left, sizeof(t.left)) != cudaSuccess) return MPHF_ENOMEM;
     if (cudaMemcpy(d.tau, t.tau, sizeof(t.tau), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d.nodes, t.nodes, sizeof(t.nodes), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.fixed, t.fixed, sizeof(t.fixed), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(d.fixed, t.fixed, sizeof(t.fixed), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d.left, t.left, sizeof(t.left), cudaMemcpyHostToDevice) != cudaSuccess)
         return MPHF_ECUDA;
+    int rc = device_mod_tables(dev, &d.mod_c, &d.mod_M);
+    if (rc != MPHF_OK) return rc;
     cache[key] = d;
     *out = d;
     return MPHF_OK;
@@ -658,6 +689,14 @@ static QueryView view_of(const mphf_t *h) {
     q.tau = h->tabs.tau;
     q.nodes_tab = h->tabs.nodes;
     q.fixed_tab = h->tabs.fixed;
+    q.left_tab = h->tabs.left;
+    q.mod_c = h->tabs.mod_c;
+    q.mod_M = h->tabs.mod_M;
+    const Shape shp = make_shape(I.leaf_size, I.tree_shape);
+    q.lower1 = shp.lower1;
+    q.lower2 = shp.lower2;
+    q.magic_leaf = unit_magic(shp.leaf);
+    q.magic_l1 = unit_magic(shp.lower1);
     q.nb = I.nb;
     q.leaf = I.leaf_size;
     q.bij = I.leaf_bijection;

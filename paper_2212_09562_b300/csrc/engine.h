@@ -101,8 +101,13 @@ struct QueryView {
     uint32_t ef_L[2];
     const uint8_t *tau;
     const uint32_t *nodes_tab, *fixed_tab;
+    const uint16_t *left_tab;   // left part per fanout-2 node size
+    const uint32_t *mod_c;      // exact remainder constants per node size
+    const uint64_t *mod_M;
     uint64_t nb;
     uint32_t leaf, bij, key_bytes, tree;
+    uint32_t magic_leaf, magic_l1;  // ceil(2^32 / l), ceil(2^32 / lower-1 size)
+    uint32_t lower1, lower2;
 };
 void launch_query(const QueryView &q, const void *keys, uint64_t n, uint64_t *out, cudaStream_t st);
 void launch_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad,

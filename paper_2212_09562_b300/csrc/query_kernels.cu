@@ -88,8 +88,11 @@ __device__ __forceinline__ uint64_t node_value(const uint64_t *gr, uint64_t fixe
     return (u.value(gr, idx) << tau) | fixed;
 }
 
+// The walk reads every per-size constant from tables (remainder constants,
+// fanout-2 left parts, the unit divisors' magic numbers): computing them in
+// the kernel would cost 64-bit divisions at every level.
 __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out) {
-    const Shape sh = make_shape(q.leaf, q.tree);
+    const uint32_t leaf = q.leaf, lower1 = q.lower1, lower2 = q.lower2;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t *p = (const uint64_t *)keys;
@@ -111,32 +114,42 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
         UnaryCursor ucur{start + q.fixed_tab[m], 0};
         uint64_t fpos = start, idx = 0, rank = 0;
         uint32_t depth = 0;
-        while (m > sh.leaf) {
-            uint32_t t = q.tau[m];
-            uint64_t x = node_value(q.gr, fpos, t, ucur, idx);
-            uint32_t pos = make_mod(m)(mix64(lo + level_salt(salt_level(sh, m, depth)) + x));
-            uint32_t c;
-            if (m > sh.lower2)
-                c = pos < upper_left(sh, m) ? 0 : 1;
-            else
-                c = pos / lower_unit(sh, m);
+        while (m > leaf) {
+            const uint32_t t = q.tau[m];
+            const uint64_t x = node_value(q.gr, fpos, t, ucur, idx);
+            const ModRT mod{m, q.mod_c[m], q.mod_M[m]};
             fpos += t;
             idx += 1;
-            for (uint32_t j = 0; j < c; j++) {
-                uint32_t qj = part_size(sh, m, j);
-                rank += qj;
-                fpos += q.fixed_tab[qj];
-                idx += q.nodes_tab[qj];
+            if (m > lower2) {  // fanout 2: salt 3 + depth
+                const uint32_t pos = mod(mix64(lo + level_salt(3 + depth) + x));
+                const uint32_t left = q.left_tab[m];
+                if (pos < left) {
+                    m = left;
+                } else {
+                    rank += left;
+                    fpos += q.fixed_tab[left];
+                    idx += q.nodes_tab[left];
+                    m -= left;
+                }
+            } else {  // lower aggregation: children of `unit` keys, the last one smaller
+                const bool l1 = m <= lower1;
+                const uint32_t unit = l1 ? leaf : lower1;
+                const uint32_t pos = mod(mix64(lo + level_salt(l1 ? 1 : 2) + x));
+                const uint32_t c = div_unit(pos, l1 ? q.magic_leaf : q.magic_l1);
+                // every child before c is a full unit
+                rank += (uint64_t)c * unit;
+                fpos += (uint64_t)c * q.fixed_tab[unit];
+                idx += (uint64_t)c * q.nodes_tab[unit];
+                m = min(unit, m - c * unit);
             }
-            m = part_size(sh, m, c);
             depth++;
         }
         if (m <= 1) {
             out[i] = cum + rank;
             continue;
         }
-        uint64_t x = node_value(q.gr, fpos, q.tau[m], ucur, idx);
-        const ModRT mod = make_mod(m);
+        const uint64_t x = node_value(q.gr, fpos, q.tau[m], ucur, idx);
+        const ModRT mod{m, q.mod_c[m], q.mod_M[m]};
         uint64_t pos;
         if (q.bij == MPHF_BIJECTION_PLAIN) {
             pos = mod(mix64(lo + level_salt(0) + x));
@@ -149,9 +162,12 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
             const uint32_t half = (__popc(row & z) & 1) ? (uint32_t)(h >> 32) : (uint32_t)h;
             pos = mod32(mod, half);
         } else {
-            uint64_t r = x % m;
+            const uint32_t r = mod(x);  // x = k m + r
             pos = mod(mix64(lo + level_salt(0) + (x - r)));
-            if (hi & 1) pos = (pos + r) % m;
+            if (hi & 1) {  // keys of B move by r (Section 4)
+                pos += r;
+                if (pos >= m) pos -= m;
+            }
         }
         out[i] = cum + rank + pos;
     }

@@ -166,6 +166,7 @@ const SizeTables &size_tables(uint32_t leaf, uint32_t bij, uint32_t tree) {
     Shape s = make_shape(leaf, t->tree);
     for (uint32_t m = 0; m <= 4096; m++) {
         t->tau[m] = node_tau(leaf, bij, t->tree, m);
+        t->left[m] = node_kind(s, m) == NODE_UPPER ? (uint16_t)upper_left(s, m) : 0;
         if (m < 2) {
             t->nodes[m] = 0;
             t->fixed[m] = 0;
@@ -186,6 +187,21 @@ const SizeTables &size_tables(uint32_t leaf, uint32_t bij, uint32_t tree) {
     const SizeTables &ref = *t;
     cache[key] = std::move(t);
     return ref;
+}
+
+const ModTables &mod_tables() {
+    static std::once_flag once;
+    static ModTables t;
+    std::call_once(once, [] {
+        t.c[0] = 0;
+        t.M[0] = 0;
+        for (uint32_t m = 1; m <= 4096; m++) {
+            const ModRT r = make_mod(m);
+            t.c[m] = r.c;
+            t.M[m] = r.M;
+        }
+    });
+    return t;
 }
 
 }  // namespace rs

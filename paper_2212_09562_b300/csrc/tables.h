@@ -16,7 +16,16 @@ struct SizeTables {
     uint8_t tau[4097];
     uint32_t nodes[4097];
     uint32_t fixed[4097];
+    uint16_t left[4097];  // left part of a fanout-2 node of m keys (0 for other sizes)
 };
+
+// Exact remainder constants per node size m in [1, 4096] (the reduction of
+// ModRT): c[m] = 2^32 mod m, M[m] = floor((2^64 - 1) / m) + 1; index 0 unused.
+struct ModTables {
+    uint32_t c[4097];
+    uint64_t M[4097];
+};
+const ModTables &mod_tables();
 
 // Computes (or returns the cached) tables for one leaf size / leaf method.
 const SizeTables &size_tables(uint32_t leaf, uint32_t bij, uint32_t tree);
