@@ -25,16 +25,39 @@ __device__ __forceinline__ uint64_t read_bits(const uint64_t *w, uint64_t pos, u
     return len == 64 ? v : v & ((1ull << len) - 1);
 }
 
+// Position of the r-th one (0-based, r < popcount) of a word: narrow by
+// the popcounts of halves, quarters and bytes, then clear at most 7 ones.
+__device__ __forceinline__ uint32_t select_in_word(uint64_t word, uint32_t r) {
+    uint32_t pos = 0;
+    uint32_t x = (uint32_t)word, c = __popc(x);
+    if (r >= c) {
+        r -= c;
+        x = (uint32_t)(word >> 32);
+        pos = 32;
+    }
+    c = __popc(x & 0xFFFFu);
+    if (r >= c) {
+        r -= c;
+        x >>= 16;
+        pos += 16;
+    }
+    c = __popc(x & 0xFFu);
+    if (r >= c) {
+        r -= c;
+        x >>= 8;
+        pos += 8;
+    }
+    for (; r; r--) x &= x - 1;
+    return pos + (uint32_t)(__ffs(x) - 1);
+}
+
 // Position of the j-th one (0-based) at or after bit `start`.
 __device__ __forceinline__ uint64_t select_from(const uint64_t *w, uint64_t start, uint64_t j) {
     uint64_t wi = start >> 6;
     uint64_t word = w[wi] & (~0ull << (start & 63));
     for (;;) {
         uint32_t c = __popcll(word);
-        if (j < c) {
-            for (; j; j--) word &= word - 1;
-            return wi * 64 + (uint64_t)(__ffsll((long long)word) - 1);
-        }
+        if (j < c) return wi * 64 + select_in_word(word, (uint32_t)j);
         j -= c;
         word = w[++wi];
     }
@@ -55,10 +78,11 @@ __device__ __forceinline__ uint64_t ef_get(const uint64_t *low, const uint64_t *
             b = mid - 1;
     }
     uint64_t word = high[a];
-    for (uint64_t r = i - dir[a]; r; r--) word &= word - 1;
-    const uint64_t sel = a * 64 + (uint64_t)(__ffsll((long long)word) - 1);
+    const uint32_t bit = select_in_word(word, (uint32_t)(i - dir[a]));
+    const uint64_t sel = a * 64 + bit;
     if (next) {
-        word &= word - 1;  // the ones after element i's, in this word and then the next ones
+        // the ones after element i's, in this word and then the next ones
+        word = bit == 63 ? 0 : word & (~0ull << (bit + 1));
         uint64_t wi = a;
         while (!word) word = high[++wi];
         const uint64_t sel1 = wi * 64 + (uint64_t)(__ffsll((long long)word) - 1);
