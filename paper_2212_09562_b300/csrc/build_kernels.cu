@@ -869,15 +869,19 @@ struct CellLabels {
         for (int i = 1; i < NW; i++) x = r == (uint32_t)i ? w[i] : x;
         return (x >> ((c & 3) * 8)) & 0xFFu;
     }
-    // every byte equal to `from` becomes `to`
+    // every byte equal to `from` becomes `to`.  Labels are below 128, so a
+    // byte of t = w ^ from is zero iff adding 0x7F leaves its top bit clear
+    // (no carry crosses bytes); a sign-replicating byte permute turns those
+    // top bits into byte masks.
     __device__ __forceinline__ void relabel(uint32_t from, uint32_t to) {
         const uint32_t bf = from * 0x01010101u, diff = bf ^ (to * 0x01010101u);
 #pragma unroll
         for (int i = 0; i < NW; i++) {
-            const uint32_t t = w[i] ^ bf;  // zero bytes where the label is `from`
-            const uint32_t nonzero = ((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t;
-            const uint32_t zero_hi = ~nonzero & 0x80808080u;
-            w[i] ^= ((zero_hi >> 7) * 0xFFu) & diff;
+            const uint32_t t = w[i] ^ bf;
+            const uint32_t zero_hi = ~(t + 0x7F7F7F7Fu) & 0x80808080u;
+            uint32_t mask;
+            asm("prmt.b32 %0, %1, %2, 0xBA98;" : "=r"(mask) : "r"(zero_hi), "r"(0u));
+            w[i] ^= mask & diff;
         }
     }
 };
@@ -1106,6 +1110,13 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
             if constexpr (LEAF != 0) {
                 if (m == (uint32_t)LEAF) {
                     x = leaf_shock<LEAF>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
+                    done = true;
+                }
+            } else {
+                // full leaves of l = 24 (the size ShockHash makes affordable) get a
+                // compile-time copy of the leaf search without one of the whole kernel
+                if (m == 24 && d.leaf == 24) {
+                    x = leaf_shock<24>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
                     done = true;
                 }
             }
