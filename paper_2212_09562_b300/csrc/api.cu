@@ -195,8 +195,9 @@ struct mphf {
     mphf_allocator alloc{};
     bool has_alloc = false;
     uint64_t *values = nullptr, *node_off = nullptr, *cum_keys = nullptr, *bit_pos = nullptr;
-    uint64_t *gr = nullptr, *ef = nullptr, *ef_dir = nullptr;
+    uint64_t *gr = nullptr, *ef = nullptr, *ef_dir = nullptr;  // ef_dir: rank then select directories
     uint64_t ef_dir_len[2] = {0, 0};
+    uint64_t ef_sel_len = 0;
     DevTables tabs;
     mphf_stats stats{};
 };
@@ -527,9 +528,10 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         h->info.ef_words = e0.low_words + e0.high_words + e1.low_words + e1.high_words;
         h->ef_dir_len[0] = e0.high_words + 1;
         h->ef_dir_len[1] = e1.high_words + 1;
+        h->ef_sel_len = (j.nb + 1 + 63) / 64;  // one entry per 64 elements of a sequence
         h->gr = (uint64_t *)jm.get(h->info.gr_words * 8 + 8);
         h->ef = (uint64_t *)jm.get(h->info.ef_words * 8 + 8);
-        h->ef_dir = (uint64_t *)jm.get((h->ef_dir_len[0] + h->ef_dir_len[1]) * 8);
+        h->ef_dir = (uint64_t *)jm.get((h->ef_dir_len[0] + h->ef_dir_len[1] + 2 * h->ef_sel_len) * 8);
         if (!h->gr || !h->ef || !h->ef_dir) {
             fail_job(j, MPHF_ENOMEM, mem);
             continue;
@@ -542,8 +544,12 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
                  *hi1 = lo1 + e1.low_words;
         launch_ef_write(h->cum_keys, j.nb + 1, e0.L, lo0, hi0, st);
         launch_ef_write(h->bit_pos, j.nb + 1, e1.L, lo1, hi1, st);
-        launch_rank_dir(hi0, e0.high_words, h->ef_dir, scan_tmp, st);
-        launch_rank_dir(hi1, e1.high_words, h->ef_dir + h->ef_dir_len[0], scan_tmp, st);
+        uint64_t *rank0 = h->ef_dir, *rank1 = rank0 + h->ef_dir_len[0];
+        uint64_t *sel0 = rank1 + h->ef_dir_len[1], *sel1 = sel0 + h->ef_sel_len;
+        launch_rank_dir(hi0, e0.high_words, rank0, scan_tmp, st);
+        launch_rank_dir(hi1, e1.high_words, rank1, scan_tmp, st);
+        launch_select_dir(e0.high_words, rank0, sel0, st);
+        launch_select_dir(e1.high_words, rank1, sel1, st);
         launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.leaf_bijection,
                      j.p.tree_shape, j.counters, st);
         CU(cudaGetLastError());
@@ -682,6 +688,8 @@ static QueryView view_of(const mphf_t *h) {
     q.ef_high[1] = q.ef_low[1] + I.ef_seq_words[2];
     q.ef_dir[0] = h->ef_dir;
     q.ef_dir[1] = h->ef_dir + h->ef_dir_len[0];
+    q.ef_sel[0] = q.ef_dir[1] + h->ef_dir_len[1];
+    q.ef_sel[1] = q.ef_sel[0] + h->ef_sel_len;
     q.ef_high_words[0] = I.ef_seq_words[1];
     q.ef_high_words[1] = I.ef_seq_words[3];
     q.ef_L[0] = I.ef_low_bits[0];

@@ -1442,4 +1442,21 @@ void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint
     launch_exclusive_scan(dir, nwords + 1, tmp, st);
 }
 
+// Select directory of a bit vector: sel[j] = the word holding one number
+// 64 j.  Word w holds the ones dir[w] .. dir[w + 1] - 1, so it writes every
+// multiple of 64 in that range (each entry exactly once).
+__global__ void k_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel) {
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t first = dir[w], end = dir[w + 1];
+        for (uint64_t j = (first + 63) >> 6; (j << 6) < end; j++) sel[j] = w;
+    }
+}
+
+void launch_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel, cudaStream_t st) {
+    if (nwords == 0) return;
+    k_select_dir<<<grid_for(nwords, 256), 256, 0, st>>>(nwords, dir, sel);
+    note_launches(1);
+}
+
 }  // namespace rs

@@ -89,6 +89,8 @@ void launch_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low, u
 // dir[w] = ones in words [0, w), w in [0, nwords]; tmp: scan_tmp_words(nwords + 1).
 void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint64_t *tmp,
                      cudaStream_t st);
+// sel[j] = the word holding one number 64 j (0-based), from the rank directory.
+void launch_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel, cudaStream_t st);
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
                   uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st);
 
@@ -96,7 +98,8 @@ void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nod
 struct QueryView {
     const uint64_t *gr;
     const uint64_t *ef_low[2], *ef_high[2];
-    const uint64_t *ef_dir[2];
+    const uint64_t *ef_dir[2];   // ones before each high word
+    const uint64_t *ef_sel[2];   // the high word holding element 64 j, per j
     uint64_t ef_high_words[2];
     uint32_t ef_L[2];
     const uint8_t *tau;

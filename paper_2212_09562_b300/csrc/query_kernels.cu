@@ -63,20 +63,16 @@ __device__ __forceinline__ uint64_t select_from(const uint64_t *w, uint64_t star
     }
 }
 
-// Element i of an Elias-Fano sequence, select on the high bits through the
-// rank directory dir (ones before each word).  With `next` it also returns
-// element i + 1, whose high-bit one is the next one after element i's.
+// Element i of an Elias-Fano sequence.  The select directory gives the high
+// word holding element 64 floor(i / 64); the rank directory (ones before each
+// word) moves forward from there to the word holding element i, about one
+// or two words since the high bits hold about two bits per element.  With
+// `next` it also returns element i + 1, whose high-bit one is the next one.
 __device__ __forceinline__ uint64_t ef_get(const uint64_t *low, const uint64_t *high,
-                                           const uint64_t *dir, uint64_t nwords, uint32_t L,
+                                           const uint64_t *dir, const uint64_t *seldir, uint32_t L,
                                            uint64_t i, uint64_t *next = nullptr) {
-    uint64_t a = 0, b = nwords - 1;
-    while (a < b) {
-        uint64_t mid = (a + b + 1) >> 1;
-        if (dir[mid] <= i)
-            a = mid;
-        else
-            b = mid - 1;
-    }
+    uint64_t a = seldir[i >> 6];
+    while (dir[a + 1] <= i) a++;
     uint64_t word = high[a];
     const uint32_t bit = select_in_word(word, (uint32_t)(i - dir[a]));
     const uint64_t sel = a * 64 + bit;
@@ -126,10 +122,9 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
         fingerprint(w0, w1, hi, lo);
         uint64_t b = mulhi64(hi, q.nb);
         uint64_t nxt;
-        const uint64_t cum = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_high_words[0],
-                                    q.ef_L[0], b, &nxt);
-        const uint64_t start = ef_get(q.ef_low[1], q.ef_high[1], q.ef_dir[1], q.ef_high_words[1],
-                                      q.ef_L[1], b);
+        const uint64_t cum = ef_get(q.ef_low[0], q.ef_high[0], q.ef_dir[0], q.ef_sel[0], q.ef_L[0], b,
+                                    &nxt);
+        const uint64_t start = ef_get(q.ef_low[1], q.ef_high[1], q.ef_dir[1], q.ef_sel[1], q.ef_L[1], b);
         uint32_t m = (uint32_t)(nxt - cum);
         if (m > 4096) {  // not a key of the built set (or a corrupt function)
             out[i] = cum;

@@ -53,3 +53,14 @@ def test_bad_leaf_method_is_refused(torch):
     with pytest.raises(M.MPHFError) as e:
         M.MPHF.build(dkeys, 8, 100, True, leaf_method=3)
     assert e.value.code == M.EINVAL
+
+
+@pytest.mark.parametrize("method", [M.LEAF_EARLY, M.LEAF_TABLE])
+def test_shockhash_leaves_ignore_the_leaf_method(torch, method):
+    """ShockHash leaves have one search; the method of plain and rotation
+    leaves does not change them."""
+    dkeys = to_dev(torch, W.distinct_u64(30000, 5300))
+    a = M.MPHF.build(dkeys, 16, 2000, M.SHOCKHASH).host_arrays()
+    b = M.MPHF.build(dkeys, 16, 2000, M.SHOCKHASH, leaf_method=method).host_arrays()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k

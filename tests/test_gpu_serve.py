@@ -129,3 +129,25 @@ def test_destroy_with_queued_requests(torch):
     for dk, leaf in reqs:
         srv.submit(dk, leaf, 500)
     srv.close()  # finishes the queue, frees unpolled results
+
+
+def test_served_shockhash_and_fanout2_requests(torch, orc):
+    """Requests with ShockHash leaves and the fanout-2 tree, mixed with
+    rotation-fitting requests in one server, equal their plain builds."""
+    specs = [(12000, 24, M.SHOCKHASH, M.TREE_FANOUT2), (8000, 16, M.SHOCKHASH, M.TREE_RECSPLIT),
+             (9000, 12, M.ROTATION, M.TREE_RECSPLIT), (7000, 8, M.ROTATION, M.TREE_FANOUT2)]
+    keys = [dev(torch, W.distinct_u64(n, 5200 + i)) for i, (n, *_r) in enumerate(specs)]
+    srv = M.Server(executors=2, max_batch=8)
+    try:
+        tickets = [srv.submit(k, leaf, 2000, bij, tree=tree)
+                   for k, (n, leaf, bij, tree) in zip(keys, specs)]
+        res = poll_all(srv, tickets)
+        for t, k, (n, leaf, bij, tree) in zip(tickets, keys, specs):
+            status, built, _ = res[t]
+            assert status == M.OK
+            alone = M.MPHF.build(k, leaf, 2000, bij, tree=tree)
+            same(built, alone)
+            assert built.info.tree_shape == tree and built.info.leaf_bijection == bij
+            assert built.verify(k) == 0
+    finally:
+        srv.close()
