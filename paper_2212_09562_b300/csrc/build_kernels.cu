@@ -757,7 +757,6 @@ __device__ __forceinline__ uint64_t leaf_cyclic(const uint64_t *xs, const uint8_
     return best;
 }
 
-// Any two equal lo words among keys [0, m) of the block's bucket.
 // ShockHash leaf (Appendix C), one warp per leaf, one seed per lane and
 // round.  Under seed s key i has the cells c0 = lo32(h) mod m and
 // c1 = hi32(h) mod m; the keys are the edges of a multigraph on the m cells,
@@ -956,6 +955,7 @@ __device__ __noinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *
     }
 }
 
+// Any two equal lo words among keys [0, m) of the block's bucket.
 __device__ __forceinline__ bool block_has_duplicate(const uint64_t *lo, uint32_t m) {
     bool dup = false;
     for (uint32_t i = threadIdx.x; i < m && !dup; i += blockDim.x)
