@@ -757,15 +757,15 @@ __device__ __forceinline__ uint64_t leaf_cyclic(const uint64_t *xs, const uint8_
     return best;
 }
 
-// ShockHash leaf (Appendix C), one warp per leaf, one seed per lane and
-// round.  Under seed s key i has the cells c0 = lo32(h) mod m and
-// c1 = hi32(h) mod m; the keys are the edges of a multigraph on the m cells,
-// and a bijection choosing one cell per key exists iff no component gets
-// more keys than cells.  Each lane runs its own union-find over the edges
-// (shock_trial); the smallest accepted seeds of the round then get their
-// canonical bits (leaf_shock_bits) and retrieval vector (leaf_shock_solve)
-// from the whole warp, and the first with a solvable system is stored, with
-// the vector in bits MPHF_SH_BITS and up.
+// ShockHash leaf (Appendix C), one warp per leaf.  Under seed s key i has
+// the cells c0 = lo32(h) mod m and c1 = hi32(h) mod m; the keys are the
+// edges of a multigraph on the m cells, and a bijection choosing one cell
+// per key exists iff no component gets more keys than cells.  Lanes screen
+// seeds and run their own union-find over the edges (shock_trial,
+// leaf_shock); the smallest accepted seed gets its canonical bits
+// (leaf_shock_bits) and retrieval vector (leaf_shock_solve) from the whole
+// warp, and the first with a solvable system is stored, with the vector in
+// bits MPHF_SH_BITS and up.
 __device__ __forceinline__ uint32_t leaf_shock_bits(uint32_t c0, uint32_t c1, uint64_t lo, uint32_t m,
                                                     uint32_t lane) {
     const bool key = lane < m;
@@ -922,23 +922,59 @@ __device__ __forceinline__ bool shock_trial(const uint64_t *xs, uint32_t m_rt, u
 
 // Not inlined: its label registers would otherwise push the split searches
 // of the same kernel past the 64-register budget.
+// Position of the k-th set bit (0-based, k < popcount) of a 32-bit mask.
+__device__ __forceinline__ uint32_t select32(uint32_t x, uint32_t k) {
+    uint32_t pos = 0, c = __popc(x & 0xFFFFu);
+    if (k >= c) {
+        k -= c;
+        x >>= 16;
+        pos = 16;
+    }
+    c = __popc(x & 0xFFu);
+    if (k >= c) {
+        k -= c;
+        x >>= 8;
+        pos += 8;
+    }
+    for (; k; k--) x &= x - 1;
+    return pos + (uint32_t)(__ffs(x) - 1);
+}
+
+// Seeds are screened first by a necessary condition: a bijection occupies
+// every cell, so every cell must be one of some key's two cells.  With 2m
+// uniform choices all m cells are covered with probability about
+// exp(-m e^-2) (4 % at m = 24), and the screen costs only the hashes.
+// Passing seeds queue up in increasing order, one per lane; the queue gets
+// the union-find (one seed per lane) once it holds `batch` seeds, the round
+// would overflow it, or the seeds are exhausted.  The first queued seed
+// that admits a bijection and a solvable retrieval system is stored: every
+// smaller seed either failed the screen or the union-find.
+// Not inlined: its label registers would otherwise push the split searches
+// of the same kernel past the 64-register budget.
 template <uint32_t MT>
 __device__ __noinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *los, uint32_t m_rt,
-                                               const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
+                                            const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
     const uint32_t m = MT ? MT : m_rt;
     const bool key = lane < m;
     const uint64_t x = key ? xs[lane] : 0;  // lo + salt(0)
     const uint64_t lo = key ? los[lane] : 0;
     const uint64_t row_salt = level_salt(MPHF_SH_ROW_LEVEL);
     const ModRT mod = make_mod(m);
+    const uint32_t full = (1u << m) - 1;
+    // queue length that holds about one or two seeds with a bijection
+    const uint32_t batch = m >= 20 ? 32u : m >= 16 ? 8u : 4u;
     if (maxv > MPHF_SH_MASK) maxv = MPHF_SH_MASK;
-    for (uint64_t s0 = 0;; s0 += 32) {
-        const uint64_t mine = s0 + lane;
-        const bool ok = mine <= maxv && shock_trial<MT>(xs, m, mine, mx, mod);
+    uint64_t queued = 0;  // lane j: the j-th queued seed
+    uint32_t count = 0;   // queued seeds (the same in every lane)
+    // union-find on the queued seeds, then the warp's bits and solve in order
+    auto drain = [&](uint64_t &found) -> bool {
+        const bool ok = lane < count && shock_trial<MT>(xs, m, queued, mx, mod);
         uint32_t ball = __ballot_sync(0xffffffffu, ok);
-        while (ball) {  // accepted seeds, smallest first
-            const uint64_t s = s0 + (uint32_t)(__ffs(ball) - 1);
+        count = 0;
+        while (ball) {
+            const uint32_t src = __ffs(ball) - 1;
             ball &= ball - 1;
+            const uint64_t s = __shfl_sync(0xffffffffu, queued, src);
             uint32_t hl, hh;
             mx(x + s, hl, hh);
             const uint32_t c0 = key ? mod32(mod, hl) : 0u, c1 = key ? mod32(mod, hh) : 0u;
@@ -946,9 +982,41 @@ __device__ __noinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *
             const uint64_t r = mix64(lo + row_salt + s);
             const uint32_t row = key ? ((uint32_t)r & ((1u << m) - 1)) : 0u;
             uint32_t z;
-            if (leaf_shock_solve(row, key ? beta : 0u, m, lane, z)) return s | ((uint64_t)z << MPHF_SH_BITS);
+            if (leaf_shock_solve(row, key ? beta : 0u, m, lane, z)) {
+                found = s | ((uint64_t)z << MPHF_SH_BITS);
+                return true;
+            }
         }
-        if (s0 + 32 > maxv) {
+        return false;
+    };
+    uint64_t found = 0;
+    for (uint64_t s0 = 0;; s0 += 32) {
+        const uint64_t mine = s0 + lane;
+        bool pass = false;
+        if (mine <= maxv) {
+            uint32_t cover = 0;
+            for (uint32_t i = 0; i < m; i++) {
+                uint32_t hl, hh;
+                mx(xs[i] + mine, hl, hh);
+                if constexpr (MT != 0)
+                    cover |= (1u << (hl % MT)) | (1u << (hh % MT));
+                else
+                    cover |= (1u << mod32(mod, hl)) | (1u << mod32(mod, hh));
+            }
+            pass = cover == full;
+        }
+        const uint32_t pb = __ballot_sync(0xffffffffu, pass);
+        const uint32_t np = __popc(pb);
+        const bool last = s0 + 32 > maxv;
+        if (count + np > 32 && drain(found)) return found;
+        // append this round's passing seeds behind the queue, in seed order
+        const uint32_t t = lane - count;  // rank of the seed this lane receives
+        const uint32_t src = (lane >= count && t < np) ? select32(pb, t) : 0u;
+        const uint64_t v = __shfl_sync(0xffffffffu, mine, src);
+        if (lane >= count && t < np) queued = v;
+        count += np;
+        if ((count >= batch || (last && count)) && drain(found)) return found;
+        if (last) {
             limit = true;
             return 0;
         }
