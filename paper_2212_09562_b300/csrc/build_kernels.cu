@@ -961,8 +961,10 @@ __device__ __noinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *
     const uint64_t row_salt = level_salt(MPHF_SH_ROW_LEVEL);
     const ModRT mod = make_mod(m);
     const uint32_t full = (1u << m) - 1;
-    // queue length that holds about one or two seeds with a bijection
-    const uint32_t batch = m >= 20 ? 32u : m >= 16 ? 8u : 4u;
+    // queue length: screening past the answer costs more than union-find
+    // rounds with idle lanes (measured on l = 24: 8 seeds 28.3 ms, 16 30.8,
+    // 32 39.0, 4 29.1 per 10^7 keys)
+    const uint32_t batch = m >= 16 ? 8u : 4u;
     if (maxv > MPHF_SH_MASK) maxv = MPHF_SH_MASK;
     uint64_t queued = 0;  // lane j: the j-th queued seed
     uint32_t count = 0;   // queued seeds (the same in every lane)
