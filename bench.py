@@ -39,9 +39,9 @@ WORKLOAD = "rot_l16"
 OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # DRAM bytes the search kernel moves per key (lo word and rotation bit read
 # once per bucket), from dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture of k_search on 1,200,000 keys of rot_l16: 11,084,032 B.  The
+# ncu capture of k_search on 600,000 keys of rot_l16: 6,330,368 B.  The
 # traffic of a launch grows with its key count.
-SEARCH_DRAM_BYTES_PER_KEY = 11_084_032 / 1_200_000
+SEARCH_DRAM_BYTES_PER_KEY = 6_330_368 / 600_000
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 SMS, SMSP_PER_SM, LANES, SM_MAX_MHZ = 148, 4, 32, 2032.0
 PEAK_INT_OPS = SMS * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6  # issue-slot bound, lane-ops/s
@@ -395,7 +395,7 @@ def run_ours(args):
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_INT_OPS / 1e12,
             "unit": "Tintops/s", "frac": achieved / PEAK_INT_OPS,
             "traffic": (SEARCH_DRAM_BYTES_PER_KEY * w.n if w.name.startswith("rot_l16") else None),
-            "traffic_basis": "ncu DRAM bytes of k_search at 1.2e6 keys of rot_l16, scaled by n",
+            "traffic_basis": "ncu DRAM bytes of k_search at 6e5 keys of rot_l16, scaled by n",
             "kernel": "k_search", "ops_per_eval": OPS_PER_EVAL,
             "evals_per_launch": evals_per_build, "launch_ms": mean_search,
             "peak_basis": "148 SMs x 4 SMSP x 32 lanes x 2032 MHz (integer issue slots)"}

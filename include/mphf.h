@@ -76,8 +76,10 @@ typedef struct {
  *   max_value        largest value any node may store; a node that needs
  *                    more fails the build with MPHF_ESEARCH_LIMIT.
  *   threads_per_block, blocks_per_sm
- *                    launch shape of the search kernel; 0 = the tuned or
- *                    default choice.
+ *                    launch shape of the search kernel; 0 = the default:
+ *                    512 threads when a build of the launch has lower
+ *                    aggregation levels with l >= 14, else 256, and as many
+ *                    blocks per SM as fit.
  *   tree_shape       MPHF_TREE_RECSPLIT: leaves under two lower aggregation
  *                    levels with fanouts f1, f2 of l, fanout 2 above (Section
  *                    2.2, "Splitting Trees"); MPHF_TREE_FANOUT2: fanout 2 for

@@ -22,7 +22,7 @@ from . import mphf as M
 from . import workloads as W
 
 CANDIDATES = [(128, 0), (256, 0), (512, 0), (256, 2), (512, 1)]
-DEFAULT = (0, 0)  # library default (512 threads, as many blocks as fit)
+DEFAULT = (0, 0)  # library default (512 or 256 threads by tree and leaf size, as many blocks as fit)
 
 
 def cache_path() -> str:
@@ -57,8 +57,8 @@ def tune(leaf: int, rotation: bool = True, n: int | None = None, bucket: int = 2
          candidates=CANDIDATES, save: bool = True) -> dict:
     """Times every candidate shape on one build of n keys; returns the result record."""
     import torch
-    if n is None:  # about four waves of buckets at the default shape for big leaves
-        n = 600_000 if leaf >= 16 else 3_000_000
+    if n is None:  # 1500 buckets of 2000 keys: five waves at the default shape, so the tail
+        n = 3_000_000  # of the last wave does not decide (at 300 buckets it did)
     keys = torch.from_numpy(W.distinct_u64(n, 4711 + leaf).view(np.int64)).cuda()
     M.MPHF.build(keys[: min(n, 20_000)], leaf, bucket, rotation).close()  # warm-up
     times, ref = {}, None

@@ -329,6 +329,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     uint64_t max_nb = 0, total_items = 0, total_slots = 0;
     uint32_t max_m = 0;
+    bool wide_lower = false;  // some build has lower-level nodes of l >= 14
     float ms[4] = {0, 0, 0, 0};
 #define CU(x)                    \
     do {                         \
@@ -460,6 +461,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         hinst.push_back(d);
         total_items += j.nb;
         max_m = mm > max_m ? mm : max_m;
+        if (j.p.tree_shape == MPHF_TREE_RECSPLIT && j.p.leaf_size >= 14) wide_lower = true;
     }
     if (total_slots > 0xFFFFFFFFull) {
         grc = MPHF_EINVAL;
@@ -480,6 +482,12 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
             Job &j = jobs[inst_job[k]];
             launch_items_by_size(j.h->cum_keys, j.nb, size_hist, size_cursor, items, (uint32_t)k, st);
         }
+        // Default block size: the lower-level nodes of l >= 14 need hundreds of
+        // thousands of trials and fill 512 threads; smaller leaves and the
+        // fanout-2 tree do better with 256 (B300: l = 8 0.19 vs 0.30 ms,
+        // l = 12 15.6 both, fanout-2 l = 24 24.8 vs 28.3 ms; l = 16 8.85 s at
+        // 512 threads, two blocks per SM, against 9.22 s with one).
+        if (!threads) threads = wide_lower ? 512u : 256u;
         SearchLaunch L = plan_search_launch(max_m, (uint32_t)total_slots, threads, blocks_per_sm);
         cudaEventRecord(ev[2], st);
         launch_search(d_inst, items, (uint32_t)total_slots, head, L, st);
