@@ -451,6 +451,8 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         d.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
         d.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
         d.leaf_method = j.p.leaf_method;
+        d.mod_c = h->tabs.mod_c;
+        d.mod_M = h->tabs.mod_M;
         d.rot_canon = d.rot_period = nullptr;
         if (j.p.leaf_method == MPHF_LEAF_TABLE &&
             device_rot_tables(h->device, &d.rot_canon, &d.rot_period) != MPHF_OK) {

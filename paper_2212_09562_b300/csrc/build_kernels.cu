@@ -953,13 +953,13 @@ __device__ __forceinline__ uint32_t select32(uint32_t x, uint32_t k) {
 // of the same kernel past the 64-register budget.
 template <uint32_t MT>
 __device__ __noinline__ uint64_t leaf_shock(const uint64_t *xs, const uint64_t *los, uint32_t m_rt,
-                                            const Mixer &mx, uint64_t maxv, bool &limit, uint32_t lane) {
+                                            ModRT mod, const Mixer &mx, uint64_t maxv,
+                                            bool &limit, uint32_t lane) {
     const uint32_t m = MT ? MT : m_rt;
     const bool key = lane < m;
     const uint64_t x = key ? xs[lane] : 0;  // lo + salt(0)
     const uint64_t lo = key ? los[lane] : 0;
     const uint64_t row_salt = level_salt(MPHF_SH_ROW_LEVEL);
-    const ModRT mod = make_mod(m);
     const uint32_t full = (1u << m) - 1;
     // queue length: screening past the answer costs more than union-find
     // rounds with idle lanes (measured on l = 24: 8 seeds 28.3 ms, 16 30.8,
@@ -1052,7 +1052,7 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
     const uint32_t np = num_parts(sh, m);
     uint64_t x = 0;
     bool limit = false;
-    const ModRT mrt = make_mod(m);
+    const ModRT mrt{m, d.mod_c[m], d.mod_M[m]};  // from the table: no divisions per node
     const Mixer mx{d.k30, d.k27, d.k31};
     if (kind == NODE_UPPER) {
         x = search_upper(xs, m, mrt, upper_left(sh, m), mx, d.max_value, limit, S);
@@ -1173,24 +1173,25 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
         if (lane < m) A.tlo[off + lane] = A.lo[off + lane] + salt;
         __syncwarp();
         const uint64_t *xs = A.tlo + off;
+        const ModRT mleaf{m, d.mod_c[m], d.mod_M[m]};
         bool limit = false;
         uint64_t x;
         bool done = false;
         if (d.bij == MPHF_BIJECTION_SHOCKHASH) {
             if constexpr (LEAF != 0) {
                 if (m == (uint32_t)LEAF) {
-                    x = leaf_shock<LEAF>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
+                    x = leaf_shock<LEAF>(xs, A.lo + off, m, mleaf, mx, d.max_value, limit, lane);
                     done = true;
                 }
             } else {
                 // full leaves of l = 24 (the size ShockHash makes affordable) get a
                 // compile-time copy of the leaf search without one of the whole kernel
                 if (m == 24 && d.leaf == 24) {
-                    x = leaf_shock<24>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
+                    x = leaf_shock<24>(xs, A.lo + off, m, mleaf, mx, d.max_value, limit, lane);
                     done = true;
                 }
             }
-            if (!done) x = leaf_shock<0>(xs, A.lo + off, m, mx, d.max_value, limit, lane);
+            if (!done) x = leaf_shock<0>(xs, A.lo + off, m, mleaf, mx, d.max_value, limit, lane);
         } else if (d.leaf_method == 0) {  // lock-step: every lane hashes all m keys per trial
             uint32_t bmask = 0;
             for (uint32_t i = 0; i < m; i++) bmask |= (uint32_t)A.bb[off + i] << i;
@@ -1202,8 +1203,8 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
                 }
             }
             if (!done)
-                x = d.bij ? leaf_rotation<0>(xs, bmask, m, make_mod(m), mx, d.max_value, limit, lane)
-                               : leaf_plain<0>(xs, m, make_mod(m), mx, d.max_value, limit, lane);
+                x = d.bij ? leaf_rotation<0>(xs, bmask, m, mleaf, mx, d.max_value, limit, lane)
+                               : leaf_plain<0>(xs, m, mleaf, mx, d.max_value, limit, lane);
         } else {  // early rejection (1), with the rotation lookup table (2)
             const bool use_lut = d.leaf_method == 2 && m <= 16 && d.rot_canon;
             const uint8_t *canon = use_lut ? d.rot_canon + ((1u << m) - 4) : nullptr;
@@ -1216,8 +1217,8 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
                 }
             }
             if (!done)
-                x = d.bij ? leaf_cyclic<true>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, canon, period)
-                               : leaf_cyclic<false>(xs, A.bb + off, m, make_mod(m), mx, d.max_value, limit, lane, nullptr, nullptr);
+                x = d.bij ? leaf_cyclic<true>(xs, A.bb + off, m, mleaf, mx, d.max_value, limit, lane, canon, period)
+                               : leaf_cyclic<false>(xs, A.bb + off, m, mleaf, mx, d.max_value, limit, lane, nullptr, nullptr);
         }
         if (lane == 0) {
             if (limit) {

@@ -28,6 +28,8 @@ struct InstDesc {
     uint32_t leaf_method;        // 0 lock-step, 1 early rejection, 2 early rejection + table
     const uint8_t *rot_canon;    // per m <= 16 at offset 2^m - 4: canonical rotation of x
     const uint8_t *rot_period;   // same layout: rotation period of x
+    const uint32_t *mod_c;       // exact remainder constants per node size (ModRT)
+    const uint64_t *mod_M;
 };
 
 // One unit of work: a bucket of an instance (inst = all ones: an empty slot).
