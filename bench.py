@@ -39,9 +39,9 @@ WORKLOAD = "rot_l16"
 OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # DRAM bytes the search kernel moves per key (lo word and rotation bit read
 # once per bucket), from dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture of k_search on 600,000 keys of rot_l16: 6,330,368 B.  The
+# ncu capture of k_search on 600,000 keys of rot_l16: 6,386,432 B.  The
 # traffic of a launch grows with its key count.
-SEARCH_DRAM_BYTES_PER_KEY = 6_330_368 / 600_000
+SEARCH_DRAM_BYTES_PER_KEY = 6_386_432 / 600_000
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 SMS, SMSP_PER_SM, LANES, SM_MAX_MHZ = 148, 4, 32, 2032.0
 PEAK_INT_OPS = SMS * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6  # issue-slot bound, lane-ops/s
@@ -58,11 +58,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the key count (profiling runs)")
-    ap.add_argument("--mode", choices=["build", "serve"], default="build")
+    ap.add_argument("--mode", choices=["build", "serve", "batch"], default="build")
     ap.add_argument("--requests", type=int, default=24, help="serve mode: requests per run")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: Poisson arrivals per second")
     ap.add_argument("--batch-builds", type=int, default=128,
-                    help="builds in the batched-vs-plain comparison (0 = skip)")
+                    help="builds in the batched-vs-plain comparison (0 = skip); batch mode: 4096")
+    ap.add_argument("--batch-max-exp", type=float, default=6.0,
+                    help="batch mode: key counts floor(10^U(3, this))")
     return ap.parse_args()
 
 
@@ -151,10 +153,10 @@ def cpu_baseline(w, keys, budget_s: float) -> dict:
             "seconds": dt, "trials_per_s": trials / dt}
 
 
-def batch_vs_plain(M, torch, count: int) -> dict:
-    """The same independent builds (batch workload distribution, sizes 10^3..10^5)
-    through one batched call and through one call per build."""
-    inst = W.batch_instances(count=count, lo_exp=3.0, hi_exp=5.0)
+def batch_vs_plain(M, torch, count: int, hi_exp: float = 5.0) -> dict:
+    """The same independent builds (batch workload distribution, sizes
+    10^3..10^hi_exp) through one batched call and through one call per build."""
+    inst = W.batch_instances(count=count, lo_exp=3.0, hi_exp=hi_exp)
     keys = [torch.from_numpy(W.distinct_u64(x.n, x.seed).view(np.int64)).cuda() for x in inst]
     leaves = [x.leaf for x in inst]
     total = sum(x.n for x in inst)
@@ -174,7 +176,8 @@ def batch_vs_plain(M, torch, count: int) -> dict:
                     for a, b in zip(batched, plain))
     for g in batched + plain:
         g.close()
-    return {"builds": count, "keys": total, "sizes": "floor(10^U(3,5)), leaf in {8,12,16}, b=2000",
+    return {"builds": count, "keys": total,
+            "sizes": f"floor(10^U(3,{hi_exp:g})), leaf in {{8,12,16}}, b=2000",
             "batched_keys_per_s": total / t_batch, "plain_keys_per_s": total / t_plain,
             "batched_over_plain": t_plain / t_batch, "identical": identical}
 
@@ -239,6 +242,28 @@ def run_serve(args):
                       "sizes": "floor(10^U(4,7)) 16-byte keys", "executors": 2},
            "offered_rate": offered, "paced_at_0.8x_capacity": dict(paced, rate_per_s=rate2),
            "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """Batched workload: independent builds with log-uniform key counts and a
+    leaf size drawn per build, through one mphf_build_batch call and through
+    one build call each; identical outputs checked."""
+    import torch
+    from paper_2212_09562_b300 import mphf as M
+    M.lib()
+    count = args.batch_builds if args.batch_builds != 128 else 4096
+    sampler = ClockSampler(0)
+    sampler.start()
+    r = batch_vs_plain(M, torch, count, args.batch_max_exp)
+    clocks = sampler.stop()
+    out = {"metric": "batched MPHF build keys/s (b=2000, leaf in {8,12,16}, rotation fitting)",
+           "value": r["batched_keys_per_s"], "unit": "keys/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+           "config": {"workload": "batch", "builds": r["builds"], "keys": r["keys"],
+                      "sizes": r["sizes"]},
+           "plain_keys_per_s": r["plain_keys_per_s"], "batched_over_plain": r["batched_over_plain"],
+           "identical": r["identical"], "clocks": clocks}
     print(json.dumps(out), flush=True)
 
 
@@ -427,6 +452,8 @@ def main():
         run_reference(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 
