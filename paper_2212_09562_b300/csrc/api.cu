@@ -700,8 +700,6 @@ static QueryView view_of(const mphf_t *h) {
     q.ef_dir[1] = h->ef_dir + h->ef_dir_len[0];
     q.ef_sel[0] = q.ef_dir[1] + h->ef_dir_len[1];
     q.ef_sel[1] = q.ef_sel[0] + h->ef_sel_len;
-    q.ef_high_words[0] = I.ef_seq_words[1];
-    q.ef_high_words[1] = I.ef_seq_words[3];
     q.ef_L[0] = I.ef_low_bits[0];
     q.ef_L[1] = I.ef_low_bits[1];
     q.tau = h->tabs.tau;

@@ -102,7 +102,6 @@ struct QueryView {
     const uint64_t *ef_low[2], *ef_high[2];
     const uint64_t *ef_dir[2];   // ones before each high word
     const uint64_t *ef_sel[2];   // the high word holding element 64 j, per j
-    uint64_t ef_high_words[2];
     uint32_t ef_L[2];
     const uint8_t *tau;
     const uint32_t *nodes_tab, *fixed_tab;
