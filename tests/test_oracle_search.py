@@ -71,7 +71,7 @@ def test_plain_leaf_trials_match_l_to_the_l_over_l_factorial(orc):
     assert abs(mean - expected) < 4.5 * se, (mean, expected, se)
 
 
-@pytest.mark.parametrize("leaf,count", [(8, 6000), (12, 1500)])
+@pytest.mark.parametrize("leaf,count", [(8, 6000), (12, 1500), (16, 800)])
 def test_rotation_leaf_trials_match_exact_enumeration(orc, leaf, count):
     m = leaf
     expected = sum(math.comb(m, a) * 2.0**-m / exact_rotation_success(m, a) for a in range(m + 1))
@@ -81,6 +81,8 @@ def test_rotation_leaf_trials_match_exact_enumeration(orc, leaf, count):
         assert expected == pytest.approx(56.481, rel=1e-4)
     if leaf == 12:
         assert expected == pytest.approx(1575.40, rel=1e-4)
+    if leaf == 16:  # the benchmark's leaf size
+        assert expected == pytest.approx(55239.48, rel=1e-5)
 
 
 @pytest.mark.parametrize("leaf,m,depth,count", [(8, 32, 0, 3000), (8, 96, 0, 1500), (8, 20, 0, 3000),
