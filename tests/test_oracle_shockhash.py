@@ -187,9 +187,9 @@ def test_shockhash_leaf_is_minimal_by_brute_force(orc, m):
         assert all(chk.accepts(lo, t, m) is None for t in range(s))
 
 
-def test_shockhash_trials_match_the_success_probability(orc):
-    rng = np.random.default_rng(61)
-    m, count = 8, 3000
+@pytest.mark.parametrize("m,count,seed", [(8, 3000, 61), (16, 6000, 901), (24, 600, 85)])
+def test_shockhash_trials_match_the_success_probability(orc, m, count, seed):
+    rng = np.random.default_rng(seed)
     t = []
     for _ in range(count):
         lo = rng.integers(0, 2**63, m, dtype=np.int64).astype(np.uint64)
