@@ -15,7 +15,10 @@
  *     a device-side error code (build, verify) synchronise the stream
  *     before returning; mphf_query does not.
  *   - Keys are caller-owned, 8-byte aligned, and must stay valid until the
- *     call returns.
+ *     call returns.  A misaligned key or output pointer gives MPHF_EINVAL
+ *     before any device work.
+ *   - A function lives on the device that was current when it was built;
+ *     query and verify it with that device current (else MPHF_EINVAL).
  *     A key is 8 bytes (one little-endian 64-bit word) or 16 bytes (two
  *     words, the first is w0).  Keys must be distinct.
  *   - Everything a build allocates belongs to the returned mphf_t and is
@@ -161,13 +164,17 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *param
                   mphf_t **out);
 
 /* Same as mphf_build_ex with the keys in host memory: the keys are copied
- * to the device inside the call (pinned host memory gives the fastest copy). */
+ * to the device inside the call (pinned host memory gives the fastest copy).
+ * The parameters and n are checked before anything is allocated or copied. */
 int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *params,
                     void *stream, mphf_t **out);
 
 /* Evaluates h on n keys (Section 2.2, "Query"; Section 4 for the rotation
- * of the keys in B; Appendix C for the retrieved cell of a ShockHash leaf).  d_out[i] = h(key i) in [0, n_built) for keys of the
- * built set.  Asynchronous on the stream. */
+ * of the keys in B; Appendix C for the retrieved cell of a ShockHash leaf).
+ * d_out[i] = h(key i) in [0, n_built) for keys of the built set; d_out holds
+ * n 8-byte-aligned words.  Asynchronous on the stream.  Errors: MPHF_EINVAL
+ * for a NULL or misaligned pointer with n > 0, a function with no keys, or
+ * another device current than the function's. */
 int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out, void *stream);
 
 /* Checks on the device that h maps the n keys at d_keys bijectively onto
@@ -224,6 +231,8 @@ int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t tree_sh
  * Elias-Fano words.  With h_buf NULL, *len receives the size needed. */
 int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream);
 
+/* Releases h.  Synchronises h's device first (queries of h may still be in
+ * flight on any stream); the current device is left as it was. */
 int mphf_free(mphf_t *h);
 
 const char *mphf_strerror(int code);

@@ -51,13 +51,18 @@ int device_mod_tables(int dev, uint32_t **c, uint64_t **M) {
         const ModTables &t = mod_tables();
         uint32_t *dc = nullptr;
         uint64_t *dM = nullptr;
-        if (cudaMalloc(&dc, sizeof(t.c)) != cudaSuccess || cudaMalloc(&dM, sizeof(t.M)) != cudaSuccess) {
+        int rc = MPHF_OK;
+        if (cudaMalloc(&dc, sizeof(t.c)) != cudaSuccess || cudaMalloc(&dM, sizeof(t.M)) != cudaSuccess)
+            rc = MPHF_ENOMEM;
+        else if (cudaMemcpy(dc, t.c, sizeof(t.c), cudaMemcpyHostToDevice) != cudaSuccess ||
+                 cudaMemcpy(dM, t.M, sizeof(t.M), cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = MPHF_ECUDA;
+        if (rc != MPHF_OK) {
             cudaGetLastError();
-            return MPHF_ENOMEM;
+            cudaFree(dc);
+            cudaFree(dM);
+            return rc;
         }
-        if (cudaMemcpy(dc, t.c, sizeof(t.c), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(dM, t.M, sizeof(t.M), cudaMemcpyHostToDevice) != cudaSuccess)
-            return MPHF_ECUDA;
         it = cache.emplace(dev, std::make_pair(dc, dM)).first;
     }
     *c = it->second.first;
@@ -78,17 +83,24 @@ int device_tables(int dev, uint32_t leaf, uint32_t bij, uint32_t tree, DevTables
     }
     const SizeTables &t = size_tables(leaf, bij, tree);
     DevTables d;
-    if (cudaMalloc(&d.tau, sizeof(t.tau)) != cudaSuccess) return MPHF_ENOMEM;
-    if (cudaMalloc(&d.nodes, sizeof(t.nodes)) != cudaSuccess) return MPHF_ENOMEM;
-    if (cudaMalloc(&d.fixed, sizeof(t.fixed)) != cudaSuccess) return MPHF_ENOMEM;
-    if (cudaMalloc(&d.left, sizeof(t.left)) != cudaSuccess) return MPHF_ENOMEM;
-    if (cudaMemcpy(d.tau, t.tau, sizeof(t.tau), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.nodes, t.nodes, sizeof(t.nodes), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.fixed, t.fixed, sizeof(t.fixed), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d.left, t.left, sizeof(t.left), cudaMemcpyHostToDevice) != cudaSuccess)
-        return MPHF_ECUDA;
-    int rc = device_mod_tables(dev, &d.mod_c, &d.mod_M);
-    if (rc != MPHF_OK) return rc;
+    int rc = MPHF_OK;
+    if (cudaMalloc(&d.tau, sizeof(t.tau)) != cudaSuccess || cudaMalloc(&d.nodes, sizeof(t.nodes)) != cudaSuccess ||
+        cudaMalloc(&d.fixed, sizeof(t.fixed)) != cudaSuccess || cudaMalloc(&d.left, sizeof(t.left)) != cudaSuccess)
+        rc = MPHF_ENOMEM;
+    else if (cudaMemcpy(d.tau, t.tau, sizeof(t.tau), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(d.nodes, t.nodes, sizeof(t.nodes), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(d.fixed, t.fixed, sizeof(t.fixed), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(d.left, t.left, sizeof(t.left), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = MPHF_ECUDA;
+    if (rc == MPHF_OK) rc = device_mod_tables(dev, &d.mod_c, &d.mod_M);
+    if (rc != MPHF_OK) {  // nothing is cached: free what this call allocated
+        cudaGetLastError();
+        cudaFree(d.tau);
+        cudaFree(d.nodes);
+        cudaFree(d.fixed);
+        cudaFree(d.left);
+        return rc;
+    }
     cache[key] = d;
     *out = d;
     return MPHF_OK;
@@ -126,13 +138,18 @@ int device_rot_tables(int dev, const uint8_t **canon, const uint8_t **period) {
         }
     }
     uint8_t *dc = nullptr, *dp = nullptr;
-    if (cudaMalloc(&dc, total) != cudaSuccess || cudaMalloc(&dp, total) != cudaSuccess) {
+    int rc = MPHF_OK;
+    if (cudaMalloc(&dc, total) != cudaSuccess || cudaMalloc(&dp, total) != cudaSuccess)
+        rc = MPHF_ENOMEM;
+    else if (cudaMemcpy(dc, c.data(), total, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(dp, pr.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = MPHF_ECUDA;
+    if (rc != MPHF_OK) {
         cudaGetLastError();
-        return MPHF_ENOMEM;
+        cudaFree(dc);
+        cudaFree(dp);
+        return rc;
     }
-    if (cudaMemcpy(dc, c.data(), total, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dp, pr.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
-        return MPHF_ECUDA;
     cache[dev] = {dc, dp};
     *canon = dc;
     *period = dp;
@@ -202,9 +219,11 @@ struct mphf {
     mphf_stats stats{};
 };
 
-static void release(mphf_t *h) {
+// Frees a handle's arrays in the order of stream st (the build's stream while
+// a build fails; the legacy stream after a device synchronisation otherwise).
+static void release(mphf_t *h, cudaStream_t st) {
     if (!h) return;
-    Mem mem{h->has_alloc ? &h->alloc : nullptr, 0};
+    Mem mem{h->has_alloc ? &h->alloc : nullptr, st};
     void *ptrs[] = {h->values, h->node_off, h->cum_keys, h->bit_pos, h->gr, h->ef, h->ef_dir};
     for (void *p : ptrs) mem.put(p);
     delete h;
@@ -274,11 +293,12 @@ struct Job {
     uint64_t n_nodes = 0;
 };
 
-int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
+// Parameters of a build apart from where its keys are.
+int check_shape(uint64_t n, const mphf_build_params *p) {
     if (!p) return MPHF_EINVAL;
     if (p->leaf_size < 2 || p->leaf_size > MPHF_MAX_LEAF || p->bucket_size < 1 ||
         p->bucket_size > MPHF_MAX_BUCKET_SIZE || (p->key_bytes != 8 && p->key_bytes != 16) ||
-        n >= (1ull << 32) || (n > 0 && !d_keys) || ((uintptr_t)d_keys & 7))
+        n >= (1ull << 32))
         return MPHF_EINVAL;
     if (p->threads_per_block &&
         (p->threads_per_block % 32 || p->threads_per_block > 512 || p->threads_per_block < 64))
@@ -287,6 +307,11 @@ int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
         p->tree_shape > MPHF_TREE_FANOUT2)
         return MPHF_EINVAL;
     return MPHF_OK;
+}
+
+int check_params(const void *d_keys, uint64_t n, const mphf_build_params *p) {
+    if ((n > 0 && !d_keys) || ((uintptr_t)d_keys & 7)) return MPHF_EINVAL;
+    return check_shape(n, p);
 }
 
 void free_job_scratch(Job &j, Mem &mem) {
@@ -308,7 +333,7 @@ void fail_job(Job &j, int rc, Mem &mem) {
     if (j.rc == MPHF_OK) j.rc = rc;
     free_job_scratch(j, mem);
     if (j.h) {
-        release(j.h);
+        release(j.h, mem.st);
         j.h = nullptr;
     }
 }
@@ -637,7 +662,7 @@ void start_job(Job &j, const void *d_keys, uint64_t n, const mphf_build_params &
     int rc = device_tables(h->device, p.leaf_size, h->info.leaf_bijection, h->info.tree_shape,
                            &h->tabs);
     if (rc) {
-        release(h);
+        release(h, 0);
         j.h = nullptr;
         j.rc = rc;
     }
@@ -673,8 +698,10 @@ int mphf_build(const void *d_keys, uint64_t n, uint32_t leaf_size, uint32_t buck
 
 int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *p, void *stream,
                     mphf_t **out) {
-    if (!p || !out || (n > 0 && !h_keys) || (p->key_bytes != 8 && p->key_bytes != 16))
-        return MPHF_EINVAL;
+    if (!out || (n > 0 && !h_keys)) return MPHF_EINVAL;
+    *out = nullptr;
+    int rc = check_shape(n, p);  // before copying n keys to the device
+    if (rc != MPHF_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     Mem mem{p->allocator, st};
     void *d = mem.get(n * p->key_bytes);
@@ -683,7 +710,7 @@ int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *p, 
         mem.put(d);
         return MPHF_ECUDA;
     }
-    int rc = mphf_build_ex(d, n, p, stream, out);
+    rc = mphf_build_ex(d, n, p, stream, out);
     mem.put(d);
     return rc;
 }
@@ -721,18 +748,33 @@ static QueryView view_of(const mphf_t *h) {
     return q;
 }
 
-int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out, void *stream) {
-    if (!h || (n > 0 && (!d_keys || !d_out))) return MPHF_EINVAL;
+// Checks shared by the entry points that query: keys 8-byte aligned, the
+// function built on the current device and not empty.
+static int query_args(const mphf_t *h, const void *d_keys, uint64_t n) {
+    if (!h || (n > 0 && !d_keys) || ((uintptr_t)d_keys & 7)) return MPHF_EINVAL;
     if (n == 0) return MPHF_OK;
-    if (h->info.n == 0) return MPHF_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
+    }
+    if (dev != h->device || h->info.n == 0) return MPHF_EINVAL;
+    return MPHF_OK;
+}
+
+int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out, void *stream) {
+    if (n > 0 && (!d_out || ((uintptr_t)d_out & 7))) return MPHF_EINVAL;
+    int rc = query_args(h, d_keys, n);
+    if (rc != MPHF_OK || n == 0) return rc;
     launch_query(view_of(h), d_keys, n, d_out, (cudaStream_t)stream);
     return cudaGetLastError() == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
 }
 
 int mphf_verify(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad, void *stream) {
-    if (!h || !n_bad || (n > 0 && !d_keys)) return MPHF_EINVAL;
+    if (!n_bad) return MPHF_EINVAL;
     *n_bad = 0;
-    if (n == 0) return MPHF_OK;
+    int rc0 = query_args(h, d_keys, n);
+    if (rc0 != MPHF_OK || n == 0) return rc0;
     cudaStream_t st = (cudaStream_t)stream;
     Mem mem{h->has_alloc ? &h->alloc : nullptr, st};
     uint64_t *vals = (uint64_t *)mem.get(n * 8);
@@ -829,8 +871,13 @@ int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream) {
 
 int mphf_free(mphf_t *h) {
     if (!h) return MPHF_EINVAL;
-    cudaDeviceSynchronize();
-    release(h);
+    int cur = h->device;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = h->device;
+    const int dev = h->device;
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();  // work still in flight on any stream may read these arrays
+    release(h, 0);
+    if (cur != dev) cudaSetDevice(cur);
     return MPHF_OK;
 }
 
@@ -1004,7 +1051,12 @@ int mphf_server_create(const mphf_server_cfg *cfg, mphf_server_t **out) {
         }
         S->streams.push_back(st);
     }
-    for (uint32_t w = 0; w < S->cfg.executors; w++) S->workers.emplace_back(server_worker, S, (int)w);
+    try {
+        for (uint32_t w = 0; w < S->cfg.executors; w++) S->workers.emplace_back(server_worker, S, (int)w);
+    } catch (...) {  // no thread could be started: stop the ones that were
+        mphf_server_destroy(S);
+        return MPHF_ENOMEM;
+    }
     *out = S;
     return MPHF_OK;
 }
@@ -1021,8 +1073,14 @@ int mphf_server_submit(mphf_server_t *S, const mphf_build_desc *desc, uint64_t *
     }
     r->ticket = S->next_ticket++;
     r->t.submitted = seconds_since(S->t0);
-    S->requests[r->ticket] = r;
-    S->pending.push_back(r);
+    try {
+        S->requests[r->ticket] = r;
+        S->pending.push_back(r);
+    } catch (...) {
+        S->requests.erase(r->ticket);
+        delete r;
+        return MPHF_ENOMEM;
+    }
     *ticket = r->ticket;
     S->cv_work.notify_one();
     return MPHF_OK;

@@ -62,6 +62,7 @@ extern "C" int mphf_verify_static(const mphf_t *h, const void *d_keys, uint64_t 
     if (!h || !n_bad || (n > 0 && !d_keys)) return MPHF_EINVAL;
     *n_bad = 0;
     if (n > kMaxKeys) return MPHF_EINVAL;  // more keys than the fixed scratch holds
+    if ((uintptr_t)d_keys & 7) return MPHF_EINVAL;
     if (n == 0) return MPHF_OK;
     uint64_t *base = nullptr;
     int rc = scratch_address(&base);

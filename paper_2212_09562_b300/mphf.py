@@ -194,6 +194,17 @@ def key_layout(keys) -> tuple[int, int]:
     raise ValueError("keys must be (n,) 64-bit or (n, 16) uint8 / (n, 2) 64-bit")
 
 
+def host_key_bytes(keys: np.ndarray) -> int:
+    """Key size of a host key array: (n,) of a 64-bit type, or (n, 16) uint8 / (n, 2) 64-bit."""
+    if keys.ndim == 1 and keys.itemsize == 8:
+        return 8
+    if keys.ndim == 2 and keys.dtype == np.uint8 and keys.shape[1] == 16:
+        return 16
+    if keys.ndim == 2 and keys.itemsize == 8 and keys.shape[1] == 2:
+        return 16
+    raise ValueError("host keys must be (n,) 64-bit or (n, 16) uint8 / (n, 2) 64-bit")
+
+
 def default_params() -> BuildParams:
     p = BuildParams()
     lib().mphf_default_params(ctypes.byref(p))
@@ -243,7 +254,7 @@ class MPHF:
                    stream=None, tree: int = TREE_RECSPLIT) -> "MPHF":
         """Build from keys in host memory (copied to the device inside the call)."""
         keys = np.ascontiguousarray(keys)
-        kb = 8 if keys.ndim == 1 else 16
+        kb = host_key_bytes(keys)
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
         p.leaf_bijection = bijection(rotation)
@@ -256,20 +267,29 @@ class MPHF:
         return cls(h.value)
 
     # --- evaluation ---------------------------------------------------------
+    def _count(self, keys) -> int:
+        """Number of keys in a device tensor laid out like the built function's keys."""
+        n, kb = key_layout(keys)
+        if n and kb != self.info.key_bytes:
+            raise ValueError("key size differs from the built function's")
+        return n
+
     def query(self, keys, out=None, stream=None):
         torch = _torch()
-        n, kb = key_layout(keys)
-        if kb != self.info.key_bytes:
-            raise ValueError("key size differs from the built function's")
+        n = self._count(keys)
         if out is None:
             out = torch.empty(n, dtype=torch.int64, device=keys.device)
+        elif (not out.is_cuda or out.device != keys.device or not out.is_contiguous()
+              or out.element_size() != 8 or out.numel() < n or (n and out.data_ptr() % 8)):
+            raise ValueError("out must be a contiguous 64-bit tensor of at least n elements "
+                             "on the keys' device")
         _check(lib().mphf_query(self._h, keys.data_ptr() if n else None, n,
                                 out.data_ptr() if n else None, _stream(stream)), "mphf_query")
         return out
 
     def verify(self, keys, stream=None) -> int:
         """Number of keys whose value is out of range or repeated (0 = bijection)."""
-        n, _ = key_layout(keys)
+        n = self._count(keys)
         bad = ctypes.c_uint64()
         _check(lib().mphf_verify(self._h, keys.data_ptr() if n else None, n, ctypes.byref(bad),
                                  _stream(stream)), "mphf_verify")
@@ -279,7 +299,7 @@ class MPHF:
         """Like verify(), without allocating device memory: a fixed scratch area
         reserved by the library serves every call (at most VERIFY_STATIC_MAX_KEYS
         keys; calls must not overlap on the device)."""
-        n, _ = key_layout(keys)
+        n = self._count(keys)
         bad = ctypes.c_uint64()
         _check(lib().mphf_verify_static(self._h, keys.data_ptr() if n else None, n,
                                         ctypes.byref(bad), _stream(stream)), "mphf_verify_static")
@@ -355,6 +375,8 @@ def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation=True,
                 max_value: int = 0, stream=None, tree: int = TREE_RECSPLIT) -> list[MPHF]:
     """Many independent builds in one call (see mphf_build_batch)."""
     count = len(keys_list)
+    if len(leaf_sizes) != count:
+        raise ValueError("one leaf size per key set")
     descs = (BuildDesc * max(count, 1))()
     for i, (k, l) in enumerate(zip(keys_list, leaf_sizes)):
         n, kb = key_layout(k)

@@ -69,6 +69,58 @@ def test_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.mphf_tau_table(8, 1, 2, 10, out.ctypes.data) == M.EINVAL
 
 
+def test_host_builds_check_their_parameters_before_copying_keys(lib):
+    """mphf_build_host rejects bad parameters and oversized n before it
+    allocates device memory or reads the host keys."""
+    h = ctypes.c_void_p(1)
+    keys = np.zeros(4, np.uint64)
+    p = M.default_params()
+    assert lib.mphf_build_host(keys.ctypes.data, 1 << 32, ctypes.byref(p), None,
+                               ctypes.byref(h)) == M.EINVAL
+    assert h.value is None  # *out is cleared on every failure
+    for field, value in [("leaf_size", 1), ("bucket_size", 0), ("key_bytes", 12),
+                         ("leaf_bijection", 7), ("tree_shape", 5)]:
+        q = M.default_params()
+        setattr(q, field, value)
+        assert lib.mphf_build_host(keys.ctypes.data, 4, ctypes.byref(q), None,
+                                   ctypes.byref(h)) == M.EINVAL
+    assert lib.mphf_build_host(None, 4, ctypes.byref(p), None, ctypes.byref(h)) == M.EINVAL
+    assert lib.mphf_build_host(keys.ctypes.data, 4, None, None, ctypes.byref(h)) == M.EINVAL
+
+
+def test_handle_calls_reject_null_handles_and_misaligned_keys(lib):
+    bad = ctypes.c_uint64(7)
+    n_len = ctypes.c_size_t(0)
+    assert lib.mphf_verify(None, None, 0, ctypes.byref(bad), None) == M.EINVAL
+    assert lib.mphf_verify_static(None, None, 0, ctypes.byref(bad), None) == M.EINVAL
+    assert lib.mphf_serialize(None, None, ctypes.byref(n_len), None) == M.EINVAL
+    assert lib.mphf_get_info(None, None) == M.EINVAL
+    assert lib.mphf_get_stats(None, None) == M.EINVAL
+    assert lib.mphf_free(None) == M.EINVAL
+    assert lib.mphf_server_poll(None, 1, 0, None, None, None) == M.EINVAL
+    assert lib.mphf_server_destroy(None) == M.EINVAL
+    # keys must be 8-byte aligned: checked on the host, before any device work
+    h = ctypes.c_void_p()
+    assert lib.mphf_build_ex(12, 5, ctypes.byref(M.default_params()), None,
+                             ctypes.byref(h)) == M.EINVAL
+    assert lib.mphf_query(None, 12, 5, 16, None) == M.EINVAL
+
+
+def test_binding_rejects_key_arrays_of_the_wrong_shape():
+    assert M.host_key_bytes(np.zeros(3, np.uint64)) == 8
+    assert M.host_key_bytes(np.zeros(3, np.int64)) == 8
+    assert M.host_key_bytes(np.zeros((3, 16), np.uint8)) == 16
+    assert M.host_key_bytes(np.zeros((3, 2), np.uint64)) == 16
+    for bad in (np.zeros(3, np.uint32), np.zeros((3, 8), np.uint8), np.zeros((3, 3), np.uint64),
+                np.zeros((2, 2, 2), np.uint64)):
+        with pytest.raises(ValueError):
+            M.host_key_bytes(bad)
+    with pytest.raises(ValueError):
+        M.MPHF.build_host(np.zeros(3, np.uint32), 8, 100)
+    with pytest.raises(ValueError):
+        M.build_batch([], [8])
+
+
 @pytest.mark.parametrize("leaf", list(range(2, 25)))
 @pytest.mark.parametrize("rotation", [M.PLAIN, M.ROTATION, M.SHOCKHASH])
 @pytest.mark.parametrize("tree", [M.TREE_RECSPLIT, M.TREE_FANOUT2])
