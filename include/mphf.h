@@ -17,10 +17,11 @@
  *   - Keys are caller-owned, 8-byte aligned, and must stay valid until the
  *     call returns.  A misaligned key or output pointer gives MPHF_EINVAL
  *     before any device work.
- *   - A function lives on the device that was current when it was built;
- *     query and verify it with that device current (else MPHF_EINVAL).
  *     A key is 8 bytes (one little-endian 64-bit word) or 16 bytes (two
  *     words, the first is w0).  Keys must be distinct.
+ *   - A function lives on the device that was current when it was built
+ *     or loaded; query and verify it with that device current (else
+ *     MPHF_EINVAL).
  *   - Everything a build allocates belongs to the returned mphf_t and is
  *     released by mphf_free.  Device memory comes from the allocator in the
  *     build parameters, or from cudaMallocAsync on the stream.
@@ -224,12 +225,37 @@ int mphf_get_stats(const mphf_t *h, mphf_stats *stats);
 int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t tree_shape, uint32_t max_m,
                    uint8_t *h_out);
 
-/* Copies the function to host memory: a header of 16 64-bit words (magic,
- * n, nb, leaf_size | tree_shape << 16, bucket_size, key_bytes,
- * leaf_bijection, gr_bits, gr_words, ef_words, the two Elias-Fano low-bit
- * counts, the four Elias-Fano sequence word counts) then the Golomb-Rice and
- * Elias-Fano words.  With h_buf NULL, *len receives the size needed. */
+/* Copies the function to host memory: a header of 16 64-bit words, then the
+ * Golomb-Rice and Elias-Fano words.  The header holds, in order: the magic
+ * (the ASCII bytes "RMPFPH01" in little-endian order), n, nb,
+ * leaf_size | tree_shape << 16, bucket_size, key_bytes, leaf_bijection,
+ * gr_bits, gr_words, ef_words, the two Elias-Fano low-bit counts, and the
+ * four Elias-Fano sequence word counts.  With h_buf NULL, *len receives the
+ * size needed. */
 int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream);
+
+/* Checks the len bytes at h_buf as mphf_serialize wrote them, on the host
+ * alone (no device is needed), and fills *info.  The Golomb-Rice and
+ * Elias-Fano words are the whole function (Section 2.2, "Representation"),
+ * so the check decodes all of them:
+ *   - the header's sizes must agree with one another and with len (bytes
+ *     after the function are ignored);
+ *   - both Elias-Fano sequences must decode to nb + 1 nondecreasing values,
+ *     from 0 to n (key counts, at most MPHF_MAX_BUCKET keys a bucket) and
+ *     from 0 to gr_bits (bit positions);
+ *   - each bucket's bits must hold exactly the fixed parts and unary
+ *     terminators of its nodes, in preorder.
+ * A blob that fails any check gives MPHF_EINVAL.  h_buf needs no alignment. */
+int mphf_load_info(const void *h_buf, size_t len, mphf_info *info);
+
+/* Rebuilds a function on the current device from a blob that passes
+ * mphf_load_info's checks (else MPHF_EINVAL, nothing allocated).  The node
+ * values, offsets and packed words equal the serialised function's; the
+ * per-size tables and query directories are recomputed; the statistics are
+ * zero.  Device memory comes from allocator (NULL: cudaMallocAsync on the
+ * stream).  On success *out owns the function.  Synchronises the stream. */
+int mphf_load(const void *h_buf, size_t len, const mphf_allocator *allocator, void *stream,
+              mphf_t **out);
 
 /* Releases h.  Synchronises h's device first (queries of h may still be in
  * flight on any stream); the current device is left as it was. */

@@ -195,6 +195,12 @@ EfDims ef_dims(uint64_t k, uint64_t last) {
     return d;
 }
 
+// Serialised form: a header of kHeadWords words starting with kMagic (the
+// bytes "RMPFPH01" read as a little-endian word), then the Golomb-Rice and
+// Elias-Fano words.
+constexpr size_t kHeadWords = 16;
+constexpr uint64_t kMagic = 0x3130485046504D52ull;
+
 int status_code(uint32_t st) {
     if (st & ST_BUCKET) return MPHF_EBUCKET;
     if (st & ST_DUPLICATE) return MPHF_EDUPLICATE;
@@ -838,7 +844,7 @@ int mphf_get_stats(const mphf_t *h, mphf_stats *s) {
 
 int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream) {
     if (!h || !len) return MPHF_EINVAL;
-    const size_t head = sizeof(uint64_t) * 16;
+    const size_t head = sizeof(uint64_t) * kHeadWords;
     const size_t need = head + (h->info.gr_words + h->info.ef_words) * 8;
     if (!h_buf) {
         *len = need;
@@ -848,7 +854,7 @@ int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream) {
         *len = need;
         return MPHF_EINVAL;
     }
-    uint64_t hd[16] = {0x3130485046504D52ull /* "RMPHF01" */, h->info.n, h->info.nb,
+    uint64_t hd[kHeadWords] = {kMagic, h->info.n, h->info.nb,
                        h->info.leaf_size | ((uint64_t)h->info.tree_shape << 16),
                        h->info.bucket_size, h->info.key_bytes,
                        h->info.leaf_bijection, h->info.gr_bits, h->info.gr_words,
@@ -908,6 +914,270 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
         if (rc && first == MPHF_OK) first = rc;
     }
     return first;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Loading a serialised function.  The Golomb-Rice words and the two
+// Elias-Fano sequences are the whole function (Section 2.2,
+// "Representation"); the per-size tables and the query directories are
+// recomputed.  A blob may be corrupt, and the query kernel trusts the
+// structure it walks, so the host decodes all of it first: the header's
+// sizes must agree with each other, the Elias-Fano sequences must decode to
+// bucket offsets, and every bucket's code must hold exactly its nodes'
+// fixed parts and unary terminators within its own bits.
+namespace {
+
+// Bits [pos, pos + w) of a little-endian word stream, w <= 64; the caller
+// guarantees pos + w <= 64 * (words in the stream).
+uint64_t host_bits(const uint64_t *words, uint64_t pos, uint32_t w) {
+    if (w == 0) return 0;
+    const uint64_t i = pos >> 6;
+    const uint32_t s = (uint32_t)(pos & 63);
+    uint64_t v = words[i] >> s;
+    if (s + w > 64) v |= words[i + 1] << (64 - s);
+    return w == 64 ? v : v & ((1ull << w) - 1);
+}
+
+// First set bit in [pos, end), or end.
+uint64_t next_one(const uint64_t *words, uint64_t pos, uint64_t end) {
+    while (pos < end) {
+        const uint64_t w = words[pos >> 6] >> (pos & 63);
+        if (w) {
+            const uint64_t p = pos + (uint64_t)__builtin_ctzll(w);
+            return p < end ? p : end;
+        }
+        pos = (pos | 63) + 1;
+    }
+    return end;
+}
+
+// Elias-Fano sequence of k values: low parts of L bits, then the high bit
+// vector, which must hold exactly k ones.
+bool ef_decode(const uint64_t *low, const uint64_t *high, uint64_t high_words, uint32_t L,
+               uint64_t k, std::vector<uint64_t> &out) {
+    out.assign(k, 0);
+    uint64_t i = 0;
+    for (uint64_t w = 0; w < high_words; w++) {
+        for (uint64_t x = high[w]; x; x &= x - 1) {
+            if (i == k) return false;
+            const uint64_t hv = w * 64 + (uint64_t)__builtin_ctzll(x) - i;
+            if (L && hv > (~0ull >> L)) return false;
+            out[i] = (hv << L) | host_bits(low, i * L, L);
+            i++;
+        }
+    }
+    return i == k;
+}
+
+// Node sizes of the subtree of m keys in preorder (nodes of >= 2 keys).
+void preorder_sizes(const Shape &s, uint32_t m, std::vector<uint32_t> &out) {
+    std::vector<uint32_t> stack{m};
+    while (!stack.empty()) {
+        const uint32_t q = stack.back();
+        stack.pop_back();
+        if (q < 2) continue;
+        out.push_back(q);
+        if (q > s.leaf)
+            for (uint32_t c = num_parts(s, q); c-- > 0;) stack.push_back(part_size(s, q, c));
+    }
+}
+
+// A blob decoded on the host.
+struct Decoded {
+    mphf_info info{};
+    const uint64_t *gr = nullptr, *ef = nullptr;  // inside the blob's words
+    std::vector<uint64_t> copy;                   // the blob, when the caller's buffer is unaligned
+    std::vector<uint64_t> cum, pos, node_off, values;
+};
+
+int decode_blob(const void *buf, size_t len, bool full, Decoded &d) {
+    if (!buf || len < kHeadWords * 8) return MPHF_EINVAL;
+    if ((uintptr_t)buf & 7) {
+        d.copy.assign(len / 8, 0);
+        memcpy(d.copy.data(), buf, d.copy.size() * 8);
+        buf = d.copy.data();
+    }
+    const uint64_t *hd = (const uint64_t *)buf;
+    mphf_info &I = d.info;
+    if (hd[0] != kMagic || hd[1] >= (1ull << 32) || (hd[3] >> 32) || ((hd[3] >> 16) & 0xFFFF) > 1 ||
+        (hd[3] & 0xFFFF) < 2 || (hd[3] & 0xFFFF) > MPHF_MAX_LEAF || hd[4] < 1 ||
+        hd[4] > MPHF_MAX_BUCKET_SIZE || (hd[5] != 8 && hd[5] != 16) || hd[6] > MPHF_BIJECTION_SHOCKHASH)
+        return MPHF_EINVAL;
+    I.n = hd[1];
+    I.nb = hd[2];
+    I.leaf_size = (uint32_t)(hd[3] & 0xFFFF);
+    I.tree_shape = (uint32_t)(hd[3] >> 16);
+    I.bucket_size = (uint32_t)hd[4];
+    I.key_bytes = (uint32_t)hd[5];
+    I.leaf_bijection = (uint32_t)hd[6];
+    I.gr_bits = hd[7];
+    I.gr_words = hd[8];
+    I.ef_words = hd[9];
+    const uint64_t room = (len - kHeadWords * 8) / 8;  // payload words present
+    if (I.nb != (I.n + I.bucket_size - 1) / I.bucket_size || I.gr_words > room ||
+        I.ef_words > room - I.gr_words || I.gr_words != I.gr_bits / 64 + (I.gr_bits % 64 != 0))
+        return MPHF_EINVAL;
+    const EfDims e0 = ef_dims(I.nb + 1, I.n), e1 = ef_dims(I.nb + 1, I.gr_bits);
+    if (hd[10] != e0.L || hd[11] != e1.L || hd[12] != e0.low_words || hd[13] != e0.high_words ||
+        hd[14] != e1.low_words || hd[15] != e1.high_words ||
+        I.ef_words != e0.low_words + e0.high_words + e1.low_words + e1.high_words)
+        return MPHF_EINVAL;
+    I.ef_low_bits[0] = e0.L;
+    I.ef_low_bits[1] = e1.L;
+    I.ef_seq_words[0] = e0.low_words;
+    I.ef_seq_words[1] = e0.high_words;
+    I.ef_seq_words[2] = e1.low_words;
+    I.ef_seq_words[3] = e1.high_words;
+    d.gr = hd + kHeadWords;
+    d.ef = d.gr + I.gr_words;
+    const uint64_t *lo0 = d.ef, *hi0 = lo0 + e0.low_words, *lo1 = hi0 + e0.high_words,
+                   *hi1 = lo1 + e1.low_words;
+    const uint64_t k = I.nb + 1;
+    if (!ef_decode(lo0, hi0, e0.high_words, e0.L, k, d.cum) ||
+        !ef_decode(lo1, hi1, e1.high_words, e1.L, k, d.pos))
+        return MPHF_EINVAL;
+    if (d.cum[0] != 0 || d.cum[I.nb] != I.n || d.pos[0] != 0 || d.pos[I.nb] != I.gr_bits)
+        return MPHF_EINVAL;
+    const SizeTables &t = size_tables(I.leaf_size, I.leaf_bijection, I.tree_shape);
+    const Shape s = make_shape(I.leaf_size, I.tree_shape);
+    const bool shock = I.leaf_bijection == MPHF_BIJECTION_SHOCKHASH;
+    d.node_off.assign(k, 0);
+    if (full) d.values.clear();
+    std::vector<uint32_t> sizes;
+    I.max_bucket = 0;
+    for (uint64_t b = 0; b < I.nb; b++) {
+        if (d.cum[b + 1] < d.cum[b] || d.cum[b + 1] - d.cum[b] > MPHF_MAX_BUCKET ||
+            d.pos[b + 1] < d.pos[b])
+            return MPHF_EINVAL;
+        const uint32_t m = (uint32_t)(d.cum[b + 1] - d.cum[b]);
+        const uint64_t start = d.pos[b], end = d.pos[b + 1];
+        I.max_bucket = m > I.max_bucket ? m : I.max_bucket;
+        d.node_off[b + 1] = d.node_off[b] + t.nodes[m];
+        if (end - start < (uint64_t)t.fixed[m] + t.nodes[m]) return MPHF_EINVAL;
+        sizes.clear();
+        preorder_sizes(s, m, sizes);
+        uint64_t fpos = start, upos = start + t.fixed[m];
+        for (uint32_t q : sizes) {
+            const uint32_t tq = t.tau[q];
+            const bool sh_leaf = shock && q <= I.leaf_size;
+            const uint64_t low = host_bits(d.gr, fpos, tq);
+            fpos += tq;
+            const uint64_t z = sh_leaf ? host_bits(d.gr, fpos, q) : 0;
+            fpos += sh_leaf ? q : 0;
+            const uint64_t one = next_one(d.gr, upos, end);
+            if (one == end) return MPHF_EINVAL;  // the unary code runs past its bucket
+            const uint64_t high = one - upos;
+            upos = one + 1;
+            if (tq >= 64 || high > (~0ull >> tq)) return MPHF_EINVAL;
+            const uint64_t coded = (high << tq) | low;
+            if (sh_leaf && coded > MPHF_SH_MASK) return MPHF_EINVAL;
+            if (full) d.values.push_back(sh_leaf ? coded | (z << MPHF_SH_BITS) : coded);
+        }
+        if (upos != end) return MPHF_EINVAL;  // bits left over after the last terminator
+    }
+    I.n_nodes = d.node_off[I.nb];
+    return MPHF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mphf_load_info(const void *h_buf, size_t len, mphf_info *info) {
+    if (!info) return MPHF_EINVAL;
+    Decoded d;
+    const int rc = decode_blob(h_buf, len, false, d);
+    if (rc == MPHF_OK) *info = d.info;
+    return rc;
+}
+
+int mphf_load(const void *h_buf, size_t len, const mphf_allocator *allocator, void *stream,
+              mphf_t **out) {
+    if (!out) return MPHF_EINVAL;
+    *out = nullptr;
+    Decoded d;
+    int rc = decode_blob(h_buf, len, true, d);
+    if (rc != MPHF_OK) return rc;
+    mphf_t *h = new (std::nothrow) mphf;
+    if (!h) return MPHF_ENOMEM;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MPHF_ECUDA;
+    }
+    if (allocator) {
+        h->alloc = *allocator;
+        h->has_alloc = true;
+    }
+    h->info = d.info;
+    rc = device_tables(h->device, d.info.leaf_size, d.info.leaf_bijection, d.info.tree_shape, &h->tabs);
+    if (rc != MPHF_OK) {
+        release(h, 0);
+        return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Mem mem{allocator, st};
+    const mphf_info &I = d.info;
+    const uint64_t k = I.nb + 1, hw0 = I.ef_seq_words[1], hw1 = I.ef_seq_words[3];
+    h->ef_dir_len[0] = hw0 + 1;
+    h->ef_dir_len[1] = hw1 + 1;
+    h->ef_sel_len = (k + 63) / 64;
+    h->cum_keys = (uint64_t *)mem.get(k * 8);
+    h->node_off = (uint64_t *)mem.get(k * 8);
+    h->bit_pos = (uint64_t *)mem.get(k * 8);
+    h->values = (uint64_t *)mem.get(I.n_nodes * 8);
+    h->gr = (uint64_t *)mem.get(I.gr_words * 8 + 8);
+    h->ef = (uint64_t *)mem.get(I.ef_words * 8 + 8);
+    h->ef_dir = (uint64_t *)mem.get((h->ef_dir_len[0] + h->ef_dir_len[1] + 2 * h->ef_sel_len) * 8);
+    const uint64_t tmp_words = scan_tmp_words((hw0 > hw1 ? hw0 : hw1) + 1) + 64;
+    uint64_t *tmp = (uint64_t *)mem.get(tmp_words * 8);
+    rc = MPHF_OK;
+    if (!h->cum_keys || !h->node_off || !h->bit_pos || !h->values || !h->gr || !h->ef || !h->ef_dir || !tmp) {
+        rc = MPHF_ENOMEM;
+    } else {
+        struct Copy {
+            void *dst;
+            const void *src;
+            size_t bytes;
+        } copies[] = {{h->cum_keys, d.cum.data(), k * 8},
+                      {h->node_off, d.node_off.data(), k * 8},
+                      {h->bit_pos, d.pos.data(), k * 8},
+                      {h->values, d.values.data(), I.n_nodes * 8},
+                      {h->gr, d.gr, I.gr_words * 8},
+                      {h->ef, d.ef, I.ef_words * 8}};
+        // the word after each packed array is read past the end by bit readers
+        if (cudaMemsetAsync(h->gr + I.gr_words, 0, 8, st) != cudaSuccess ||
+            cudaMemsetAsync(h->ef + I.ef_words, 0, 8, st) != cudaSuccess)
+            rc = MPHF_ECUDA;
+        for (const Copy &c : copies)
+            if (rc == MPHF_OK && c.bytes &&
+                cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = MPHF_ECUDA;
+        if (rc == MPHF_OK) {
+            const uint64_t *hi0 = h->ef + I.ef_seq_words[0];
+            const uint64_t *hi1 = hi0 + hw0 + I.ef_seq_words[2];
+            uint64_t *rank0 = h->ef_dir, *rank1 = rank0 + h->ef_dir_len[0];
+            uint64_t *sel0 = rank1 + h->ef_dir_len[1], *sel1 = sel0 + h->ef_sel_len;
+            launch_rank_dir(hi0, hw0, rank0, tmp, st);
+            launch_rank_dir(hi1, hw1, rank1, tmp, st);
+            launch_select_dir(hw0, rank0, sel0, st);
+            launch_select_dir(hw1, rank1, sel1, st);
+            if (cudaGetLastError() != cudaSuccess) rc = MPHF_ECUDA;
+        }
+        // the host arrays are read by the copies: wait before they go away
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = MPHF_ECUDA;
+    }
+    if (rc != MPHF_OK) cudaGetLastError();
+    mem.put(tmp);
+    if (rc != MPHF_OK) {
+        cudaStreamSynchronize(st);
+        release(h, st);
+        return rc;
+    }
+    *out = h;
+    return MPHF_OK;
 }
 
 }  // extern "C"

@@ -117,6 +117,8 @@ SIGNATURES = {
     "mphf_get_stats": (_I, [_P, _P]),
     "mphf_tau_table": (_I, [_U32, _U32, _U32, _U32, _P]),
     "mphf_serialize": (_I, [_P, _P, _P, _P]),
+    "mphf_load_info": (_I, [_P, ctypes.c_size_t, _P]),
+    "mphf_load": (_I, [_P, ctypes.c_size_t, _P, _P, _P]),
     "mphf_free": (_I, [_P]),
     "mphf_strerror": (ctypes.c_char_p, [_I]),
     "mphf_build_batch": (_I, [_P, _U32, _P, _P, _P]),
@@ -266,6 +268,15 @@ class MPHF:
         _check(rc, "mphf_build_host")
         return cls(h.value)
 
+    @classmethod
+    def load(cls, blob: bytes, stream=None) -> "MPHF":
+        """Rebuild a function on the current device from serialize()'s bytes
+        (checked on the host first; a corrupt blob raises MPHFError EINVAL)."""
+        _torch()
+        h = ctypes.c_void_p()
+        _check(lib().mphf_load(blob, len(blob), None, _stream(stream), ctypes.byref(h)), "mphf_load")
+        return cls(h.value)
+
     # --- evaluation ---------------------------------------------------------
     def _count(self, keys) -> int:
         """Number of keys in a device tensor laid out like the built function's keys."""
@@ -356,6 +367,14 @@ class MPHF:
             self.close()
         except Exception:
             pass
+
+
+def load_info(blob: bytes) -> Info:
+    """Sizes of a serialised function, after the same host-side checks as
+    MPHF.load (no device needed)."""
+    info = Info()
+    _check(lib().mphf_load_info(blob, len(blob), ctypes.byref(info)), "mphf_load_info")
+    return info
 
 
 def kernel_launches() -> int:

@@ -130,3 +130,24 @@ def group_by_bucket(O, keys: np.ndarray, nb: int):
     for i in range(len(keys)):
         groups.setdefault(int(b[i]), []).append(i)
     return hi, lo, groups
+
+
+BLOB_MAGIC = int.from_bytes(b"RMPFPH01", "little")
+
+
+def oracle_blob(o, leaf: int, bucket: int, key_bytes: int, bij: int, tree: int) -> bytes:
+    """The serialised form (16 header words, Golomb-Rice words, Elias-Fano
+    words, as include/mphf.h lays it out) of a function the oracle built.
+    Elias-Fano word counts of a sequence of k values ending at U with L low
+    bits: ceil(k L / 64) low words and ceil(((U >> L) + k) / 64) high words."""
+    k = o.nb + 1
+
+    def dims(last, L):
+        return (k * L + 63) // 64, ((last >> L) + k + 63) // 64
+
+    l0, h0 = dims(o.n, o.ef_L[0])
+    l1, h1 = dims(o.gr_bits, o.ef_L[1])
+    assert l0 + h0 + l1 + h1 == len(o.ef)
+    head = np.array([BLOB_MAGIC, o.n, o.nb, leaf | (tree << 16), bucket, key_bytes, bij, o.gr_bits,
+                     len(o.gr), len(o.ef), o.ef_L[0], o.ef_L[1], l0, h0, l1, h1], np.uint64)
+    return head.tobytes() + o.gr.astype(np.uint64).tobytes() + o.ef.astype(np.uint64).tobytes()

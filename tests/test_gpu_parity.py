@@ -207,3 +207,28 @@ def test_rot_l12_workload_sampled(torch, orc):
 
 def test_rot_l16_workload_sampled(torch, orc):
     _sampled_parity(torch, orc, "rot_l16", max(4, min(16, THREADS)))
+
+
+OUTSIDE = [  # (leaf, bucket, leaf method, tree, key bytes, n)
+    (8, 100, M.PLAIN, M.TREE_RECSPLIT, 8, 5000),
+    (12, 1000, M.ROTATION, M.TREE_RECSPLIT, 16, 20000),
+    (16, 300, M.ROTATION, M.TREE_RECSPLIT, 8, 3000),
+    (24, 2000, M.SHOCKHASH, M.TREE_FANOUT2, 8, 20000),
+    (12, 300, M.SHOCKHASH, M.TREE_RECSPLIT, 8, 9000),
+    (10, 500, M.PLAIN, M.TREE_FANOUT2, 16, 8000),
+    (5, 1, M.ROTATION, M.TREE_RECSPLIT, 8, 50),  # about a third of the buckets empty
+]
+
+
+@pytest.mark.parametrize("leaf,bucket,bij,tree,kb,n", OUTSIDE)
+def test_keys_outside_the_set_walk_like_the_oracle(torch, orc, leaf, bucket, bij, tree, kb, n):
+    """Section 2.2, "Query": outside S the value is arbitrary, but the walk
+    is the same definition on both sides (bucket, Elias-Fano lookups, one
+    decoded value and child per level, the leaf's position; empty and
+    one-key buckets return their key offset), so every value must agree."""
+    keys = W.random_keys(n, kb, 31 * n + leaf)
+    o = orc.build_mphf(keys, leaf, bucket, bij, threads=THREADS, tree=tree)
+    g = M.MPHF.build(to_dev(torch, keys), leaf, bucket, bij, tree=tree)
+    other = W.random_keys(100_000, kb, 977 + leaf + kb)
+    got = g.query(to_dev(torch, other)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, o.query(other))
