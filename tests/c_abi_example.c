@@ -4,8 +4,9 @@
  * Builds a function over n random 64-bit keys three ways (device keys with
  * rotation fitting, host keys, ShockHash leaves under the fanout-2 tree),
  * queries every key, checks that the values form a bijection onto [0, n),
- * and serialises the function.  Prints one line per build and exits 0 when
- * every check passes.
+ * serialises the function and loads the bytes back into a function that
+ * must answer every key the same way.  Prints one line per build and exits
+ * 0 when every check passes.
  *
  *   usage: c_abi_example [n]
  */
@@ -59,10 +60,23 @@ static int check(const char *what, mphf_t *h, const uint64_t *d_keys, uint64_t n
     void *blob = malloc(len);
     if (!blob) return 1;
     CHECK(mphf_serialize(h, blob, &len, NULL));
-    const int ok = bad == 0 && is_bijection(out, n) && info.n == n;
-    printf("%s: n=%llu nb=%llu nodes=%llu bits/key=%.3f serialised=%zu bytes bijection=%s\n", what,
-           (unsigned long long)info.n, (unsigned long long)info.nb, (unsigned long long)info.n_nodes,
-           (double)info.gr_bits / (double)n, len, ok ? "yes" : "NO");
+    /* load the bytes back: the loaded function must answer every key the same way */
+    mphf_info info2;
+    CHECK(mphf_load_info(blob, len, &info2));
+    mphf_t *h2 = NULL;
+    CHECK(mphf_load(blob, len, NULL, NULL, &h2));
+    uint64_t *out2 = (uint64_t *)malloc(n * sizeof(uint64_t));
+    if (!out2) return 1;
+    CHECK(mphf_query(h2, d_keys, n, d_out, NULL));
+    if (cudaMemcpy(out2, d_out, n * sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess) return 1;
+    CHECK(mphf_free(h2));
+    const int same = info2.n_nodes == info.n_nodes && memcmp(out, out2, n * sizeof(uint64_t)) == 0;
+    const int ok = bad == 0 && is_bijection(out, n) && info.n == n && same;
+    printf("%s: n=%llu nb=%llu nodes=%llu bits/key=%.3f serialised=%zu bytes loaded=%s bijection=%s\n",
+           what, (unsigned long long)info.n, (unsigned long long)info.nb,
+           (unsigned long long)info.n_nodes, (double)info.gr_bits / (double)n, len,
+           same ? "same" : "DIFFERENT", ok ? "yes" : "NO");
+    free(out2);
     free(blob);
     free(out);
     cudaFree(d_out);

@@ -1,7 +1,7 @@
 """The C ABI used from plain C: `tests/c_abi_example.c` compiles against
 include/mphf.h, links against the in-tree libmphf.so and the CUDA runtime,
-and (on a GPU) builds, queries, verifies and serialises functions with
-rotation-fitting and ShockHash leaves."""
+and (on a GPU) builds, queries, verifies, serialises and reloads functions
+with rotation-fitting and ShockHash leaves."""
 import os
 import shutil
 import subprocess
@@ -39,3 +39,4 @@ def test_c_example_runs(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     lines = r.stdout.strip().splitlines()
     assert lines[-1] == "ok" and sum("bijection=yes" in l for l in lines) == 3, r.stdout
+    assert sum("loaded=same" in l for l in lines) == 3, r.stdout
