@@ -60,6 +60,38 @@ class Allocator(ctypes.Structure):
     _fields_ = [("alloc", ctypes.c_void_p), ("free", ctypes.c_void_p), ("ctx", ctypes.c_void_p)]
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class TorchAllocator:
+    """mphf_allocator hooks backed by torch's caching allocator, so that the
+    library's device arrays count in torch's memory statistics and limits.
+    ``live`` is the number of blocks handed out and not yet returned.  Keep
+    the object alive while any function built with it exists (each MPHF
+    holds a reference)."""
+
+    def __init__(self):
+        torch = _torch()
+        self.live = 0
+
+        def alloc(nbytes, stream, ctx):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            except Exception:  # out of memory: the library sees NULL
+                return None
+            self.live += 1
+            return p
+
+        def free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+            self.live -= 1
+
+        self._alloc, self._free = _ALLOC_FN(alloc), _FREE_FN(free)
+        self.struct = Allocator(ctypes.cast(self._alloc, ctypes.c_void_p),
+                                ctypes.cast(self._free, ctypes.c_void_p), None)
+
+
 class BuildParams(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_uint32), ("bucket_size", ctypes.c_uint32),
                 ("key_bytes", ctypes.c_uint32), ("leaf_bijection", ctypes.c_uint32),
@@ -216,8 +248,9 @@ def default_params() -> BuildParams:
 class MPHF:
     """A function built on the device by libmphf."""
 
-    def __init__(self, handle: int):
+    def __init__(self, handle: int, allocator: "TorchAllocator | None" = None):
         self._h = ctypes.c_void_p(handle)
+        self._allocator = allocator  # frees of this function's arrays go through it
         info = Info()
         _check(lib().mphf_get_info(self._h, ctypes.byref(info)), "mphf_get_info")
         self.info = info
@@ -227,11 +260,13 @@ class MPHF:
     def build(cls, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
               max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
               blocks_per_sm: int = 0, stream=None, tuned: bool = False,
-              leaf_method: int | None = None, tree: int = TREE_RECSPLIT) -> "MPHF":
+              leaf_method: int | None = None, tree: int = TREE_RECSPLIT,
+              allocator: "TorchAllocator | None" = None) -> "MPHF":
         """rotation: True/False or PLAIN, ROTATION, SHOCKHASH (the leaf method);
         tree: TREE_RECSPLIT or TREE_FANOUT2;
         tuned=True takes the launch shape from the autotuner's cache;
-        leaf_method: LEAF_LOCKSTEP (default), LEAF_EARLY or LEAF_TABLE."""
+        leaf_method: LEAF_LOCKSTEP (default), LEAF_EARLY or LEAF_TABLE;
+        allocator: device memory hooks (default: the library's cudaMallocAsync)."""
         n, kb = key_layout(keys)
         if tuned and not threads_per_block and not blocks_per_sm:
             from .autotune import tuned as cached_shape
@@ -244,11 +279,13 @@ class MPHF:
         p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
         if leaf_method is not None:
             p.leaf_method = leaf_method
+        if allocator is not None:
+            p.allocator = ctypes.cast(ctypes.pointer(allocator.struct), ctypes.c_void_p)
         h = ctypes.c_void_p()
         rc = lib().mphf_build_ex(keys.data_ptr() if n else None, n, ctypes.byref(p),
                                  _stream(stream), ctypes.byref(h))
         _check(rc, "mphf_build_ex")
-        return cls(h.value)
+        return cls(h.value, allocator)
 
     @classmethod
     def build_host(cls, keys: np.ndarray, leaf_size: int = 16, bucket_size: int = 2000,
@@ -269,13 +306,14 @@ class MPHF:
         return cls(h.value)
 
     @classmethod
-    def load(cls, blob: bytes, stream=None) -> "MPHF":
+    def load(cls, blob: bytes, stream=None, allocator: "TorchAllocator | None" = None) -> "MPHF":
         """Rebuild a function on the current device from serialize()'s bytes
         (checked on the host first; a corrupt blob raises MPHFError EINVAL)."""
         _torch()
         h = ctypes.c_void_p()
-        _check(lib().mphf_load(blob, len(blob), None, _stream(stream), ctypes.byref(h)), "mphf_load")
-        return cls(h.value)
+        a = ctypes.byref(allocator.struct) if allocator is not None else None
+        _check(lib().mphf_load(blob, len(blob), a, _stream(stream), ctypes.byref(h)), "mphf_load")
+        return cls(h.value, allocator)
 
     # --- evaluation ---------------------------------------------------------
     def _count(self, keys) -> int:
@@ -361,6 +399,7 @@ class MPHF:
         if self._h and self._h.value:
             lib().mphf_free(self._h)
             self._h = ctypes.c_void_p()
+        self._allocator = None
 
     def __del__(self):
         try:
