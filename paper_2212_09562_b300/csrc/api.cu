@@ -892,6 +892,7 @@ uint64_t mphf_kernel_launches(void) { return launches_total(); }
 int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream, mphf_t **outs,
                      int *statuses) {
     if (count && (!descs || !outs)) return MPHF_EINVAL;
+    if (count == 0) return MPHF_OK;  // nothing to build, nothing to allocate
     std::vector<Job> jobs(count);
     for (uint32_t i = 0; i < count; i++) {
         mphf_build_params p;

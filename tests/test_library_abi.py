@@ -99,6 +99,8 @@ def test_handle_calls_reject_null_handles_and_misaligned_keys(lib):
     assert lib.mphf_free(None) == M.EINVAL
     assert lib.mphf_server_poll(None, 1, 0, None, None, None) == M.EINVAL
     assert lib.mphf_server_destroy(None) == M.EINVAL
+    assert lib.mphf_build_batch(None, 0, None, None, None) == M.OK  # an empty batch
+    assert lib.mphf_build_batch(None, 2, None, None, None) == M.EINVAL
     # keys must be 8-byte aligned: checked on the host, before any device work
     h = ctypes.c_void_p()
     assert lib.mphf_build_ex(12, 5, ctypes.byref(M.default_params()), None,
