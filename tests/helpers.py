@@ -151,3 +151,29 @@ def oracle_blob(o, leaf: int, bucket: int, key_bytes: int, bij: int, tree: int) 
     head = np.array([BLOB_MAGIC, o.n, o.nb, leaf | (tree << 16), bucket, key_bytes, bij, o.gr_bits,
                      len(o.gr), len(o.ef), o.ef_L[0], o.ef_L[1], l0, h0, l1, h1], np.uint64)
     return head.tobytes() + o.gr.astype(np.uint64).tobytes() + o.ef.astype(np.uint64).tobytes()
+
+
+def read_serialised_fixture(name: str = "serialised_l8_rotation.txt"):
+    """(params, blob bytes, keys, values) of a serialised-function fixture."""
+    params, words, pairs = {}, [], []
+    section = None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line.startswith("# params"):
+                params = {k: int(v) for k, v in (t.split("=") for t in line.split()[2:])}
+                continue
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith(("words", "keys")):
+                section = line.split()[0]
+                continue
+            if section == "words":
+                words.append(int(line, 16))
+            else:
+                k, v = line.split()
+                pairs.append((int(k, 16), int(v)))
+    blob = np.array(words, np.uint64).tobytes()
+    keys = np.array([k for k, _ in pairs], np.uint64)
+    values = np.array([v for _, v in pairs], np.uint64)
+    return params, blob, keys, values

@@ -95,3 +95,16 @@ def test_damaged_blob_is_refused_before_the_device(torch):
         M.MPHF.load(bytes(blob))
     assert e.value.code == M.EINVAL
     assert M.kernel_launches() == before
+
+
+def test_serialised_fixture_loads_and_is_what_the_gpu_writes(torch):
+    """The golden serialised function (written from the oracle alone)
+    queries to its stored values on the device, and the GPU build of the
+    same keys serialises to exactly its bytes."""
+    from helpers import read_serialised_fixture
+    p, blob, keys, values = read_serialised_fixture()
+    dkeys = to_dev(torch, keys)
+    h = M.MPHF.load(blob)
+    assert np.array_equal(h.query(dkeys).cpu().numpy().view(np.uint64), values)
+    g = M.MPHF.build(dkeys, p["leaf"], p["bucket"], p["bijection"], tree=p["tree"])
+    assert g.serialize() == blob

@@ -149,3 +149,18 @@ def test_random_damage_never_passes_unnoticed_as_a_different_shape(lib, orc):
             ok += 1
             assert (info.n, info.nb, info.n_nodes, info.gr_bits) == (o.n, o.nb, o.n_nodes, o.gr_bits)
     assert 0 < ok < 3000
+
+
+def test_serialised_fixture_is_still_what_the_oracle_writes(lib, orc):
+    """tests/golden/serialised_l8_rotation.txt pins the byte layout: the
+    oracle today writes the same words and the same values, and the
+    library's host decoder accepts them with the stored sizes."""
+    from helpers import read_serialised_fixture
+    p, blob, keys, values = read_serialised_fixture()
+    assert len(keys) == p["n"]
+    o = orc.build_mphf(keys, p["leaf"], p["bucket"], p["bijection"], tree=p["tree"])
+    assert oracle_blob(o, p["leaf"], p["bucket"], p["key_bytes"], p["bijection"], p["tree"]) == blob
+    assert np.array_equal(o.query(keys), values)
+    assert np.array_equal(np.sort(values), np.arange(p["n"], dtype=np.uint64))
+    info = M.load_info(blob)
+    assert (info.n, info.nb, info.n_nodes) == (p["n"], 3, o.n_nodes)
