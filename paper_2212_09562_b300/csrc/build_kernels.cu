@@ -1,19 +1,22 @@
 // build_kernels.cu -- device side of one or many RecSplit builds.
 //
 // Stages (Section 2.2 of Bez et al. 2212.09562, parallel form of Section 5.3):
-//   k_fp_hist   master hash of every key, bucket histogram
-//   k_plan      stored-node count per bucket (from the bucket size alone)
-//   k_scan_*    exclusive prefix sums (bucket offsets, node offsets, bits)
-//   k_scatter   keys grouped by bucket (lo word + rotation bit)
-//   k_search    persistent kernel, one block per bucket at a time: split
-//               searches of the inner nodes (all threads of the block try
-//               consecutive seeds), redistribution in shared memory, then
-//               leaf searches with one warp per leaf (plain or rotation
-//               fitting, Section 4)
-//   k_gr_*      Golomb-Rice lengths and bit writes (fixed parts, then unary
-//               parts, in preorder per bucket)
-//   k_ef_*      Elias-Fano sequences and a rank directory for select
-//   k_stats     trial / hash-evaluation counts from the stored values
+//   k_fp_hist(_blk)   master hash of every key, bucket histogram (per-block
+//                     histograms when nb <= 8192, global atomics above)
+//   k_plan            stored-node count per bucket (from the bucket size alone)
+//   k_scan_*          exclusive prefix sums (bucket offsets, node offsets, bits)
+//   k_scatter(_blk)   keys grouped by bucket (lo word + rotation bit)
+//   k_search          persistent kernel, one block per bucket at a time, largest
+//                     first: split searches of the inner nodes (lower levels:
+//                     all threads of the block try consecutive seeds; fanout-2
+//                     nodes: one seed per warp), redistribution in shared
+//                     memory, then leaf searches with one warp per leaf (plain,
+//                     rotation fitting of Section 4, or ShockHash of Appendix C)
+//   k_gr_*            Golomb-Rice lengths and bit writes (fixed parts, then unary
+//                     parts, in preorder per bucket)
+//   k_ef_write        Elias-Fano sequences; k_popcount + scan and k_select_dir
+//                     build their rank and select directories
+//   k_stats           trial / hash-evaluation counts from the stored values
 #include <cuda_runtime.h>
 #include <stdint.h>
 
