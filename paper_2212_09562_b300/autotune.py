@@ -43,28 +43,30 @@ def _device_name() -> str:
     return torch.cuda.get_device_name(torch.cuda.current_device())
 
 
-def _key(leaf: int, rotation) -> str:
-    return f"{_device_name()}|l={leaf}|rot={int(rotation)}"
+def _key(leaf: int, rotation, tree: int = M.TREE_RECSPLIT) -> str:
+    """Cache key: device name, leaf size, leaf method and (fanout-2 only) tree shape."""
+    k = f"{_device_name()}|l={leaf}|rot={M.bijection(rotation)}"
+    return k if tree == M.TREE_RECSPLIT else f"{k}|tree={int(tree)}"
 
 
-def tuned(leaf: int, rotation: bool = True) -> tuple[int, int]:
+def tuned(leaf: int, rotation: bool = True, tree: int = M.TREE_RECSPLIT) -> tuple[int, int]:
     """(threads_per_block, blocks_per_sm) from the cache, else the library default."""
-    entry = _load().get(_key(leaf, rotation))
+    entry = _load().get(_key(leaf, rotation, tree))
     return (int(entry["threads"]), int(entry["blocks_per_sm"])) if entry else DEFAULT
 
 
 def tune(leaf: int, rotation: bool = True, n: int | None = None, bucket: int = 2000,
-         candidates=CANDIDATES, save: bool = True) -> dict:
+         candidates=CANDIDATES, save: bool = True, tree: int = M.TREE_RECSPLIT) -> dict:
     """Times every candidate shape on one build of n keys; returns the result record."""
     import torch
     if n is None:  # 1500 buckets of 2000 keys: five waves at the default shape, so the tail
         n = 3_000_000  # of the last wave does not decide (at 300 buckets it did)
     keys = torch.from_numpy(W.distinct_u64(n, 4711 + leaf).view(np.int64)).cuda()
-    M.MPHF.build(keys[: min(n, 20_000)], leaf, bucket, rotation).close()  # warm-up
+    M.MPHF.build(keys[: min(n, 20_000)], leaf, bucket, rotation, tree=tree).close()  # warm-up
     times, ref = {}, None
     for threads, blocks in candidates:
         g = M.MPHF.build(keys, leaf, bucket, rotation, threads_per_block=threads,
-                         blocks_per_sm=blocks)
+                         blocks_per_sm=blocks, tree=tree)
         values = g.host_arrays()["values"]
         if ref is None:
             ref = values
@@ -78,7 +80,7 @@ def tune(leaf: int, rotation: bool = True, n: int | None = None, bucket: int = 2
            "candidates": {f"{t}x{b}": ms for (t, b), ms in sorted(times.items())}}
     if save:
         data = _load()
-        data[_key(leaf, rotation)] = rec
+        data[_key(leaf, rotation, tree)] = rec
         os.makedirs(os.path.dirname(cache_path()), exist_ok=True)
         tmp = cache_path() + f".tmp{os.getpid()}"
         with open(tmp, "w") as f:

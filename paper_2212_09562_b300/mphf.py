@@ -270,7 +270,7 @@ class MPHF:
         n, kb = key_layout(keys)
         if tuned and not threads_per_block and not blocks_per_sm:
             from .autotune import tuned as cached_shape
-            threads_per_block, blocks_per_sm = cached_shape(leaf_size, rotation)
+            threads_per_block, blocks_per_sm = cached_shape(leaf_size, rotation, tree)
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
         p.leaf_bijection = bijection(rotation)
