@@ -161,6 +161,17 @@ void mphf_default_params(mphf_build_params *p);
 int mphf_build(const void *d_keys, uint64_t n, uint32_t leaf_size, uint32_t bucket_size,
                void *stream, mphf_t **out);
 
+/* The same with every parameter explicit (mphf_build_params; start from
+ * mphf_default_params).  Keys: n keys of params->key_bytes bytes at d_keys,
+ * read only.  Errors (on any error *out is NULL and nothing stays allocated):
+ *   MPHF_EINVAL         a parameter out of range, n >= 2^32, d_keys NULL or
+ *                       not 8-byte aligned with n > 0, out or params NULL;
+ *   MPHF_ENOMEM         a device allocation failed;
+ *   MPHF_EDUPLICATE     two keys of one bucket share the fingerprint's lo
+ *                       word (equal keys, or a 2^-64 accident);
+ *   MPHF_EBUCKET        a bucket holds more than MPHF_MAX_BUCKET keys;
+ *   MPHF_ESEARCH_LIMIT  a node needs a value above max_value;
+ *   MPHF_ECUDA          a CUDA runtime call failed. */
 int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *params, void *stream,
                   mphf_t **out);
 
@@ -180,7 +191,8 @@ int mphf_query(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *d_out,
 
 /* Checks on the device that h maps the n keys at d_keys bijectively onto
  * [0, n) (queries them, marks a bitmap).  *n_bad = keys whose value was out
- * of range or already taken; 0 means a bijection.  Synchronises. */
+ * of range or already taken; 0 means a bijection.  Scratch comes from h's
+ * allocator.  Errors: those of mphf_query, MPHF_ENOMEM.  Synchronises. */
 int mphf_verify(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad, void *stream);
 
 /* The same check without allocating: it uses a fixed scratch area that the
@@ -198,6 +210,8 @@ int mphf_verify(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad
 int mphf_verify_static(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad,
                        void *stream);
 
+/* Copies h's sizes and parameters to *info (host memory).  MPHF_EINVAL if
+ * either pointer is NULL. */
 int mphf_get_info(const mphf_t *h, mphf_info *info);
 
 /* Device arrays of a built function, owned by h:
@@ -217,6 +231,8 @@ int mphf_get_values(const mphf_t *h, const uint64_t **d_values, const uint64_t *
 int mphf_get_bits(const mphf_t *h, const uint64_t **d_gr, uint64_t *gr_bits, const uint64_t **d_ef,
                   uint64_t *ef_words);
 
+/* Copies the build's search statistics and stage times (mphf_stats) to
+ * *stats; all zero for a loaded function. */
 int mphf_get_stats(const mphf_t *h, mphf_stats *stats);
 
 /* Golomb-Rice parameter per node size m in [0, max_m] as the library uses it

@@ -40,3 +40,13 @@ def test_c_example_runs(tmp_path):
     lines = r.stdout.strip().splitlines()
     assert lines[-1] == "ok" and sum("bijection=yes" in l for l in lines) == 3, r.stdout
     assert sum("loaded=same" in l for l in lines) == 3, r.stdout
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c", "c11"), ("c++", "c++11"), ("c++", "c++17")])
+def test_header_compiles_alone(tmp_path, lang, std):
+    """include/mphf.h needs nothing but the C standard headers, in C and C++."""
+    cc = shutil.which("gcc") or "cc"
+    src = tmp_path / "only_header.c"
+    src.write_text('#include "mphf.h"\nint main(void) { mphf_build_params p; (void)p; return 0; }\n')
+    subprocess.check_call([cc, "-x", lang, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)])
