@@ -164,3 +164,31 @@ def test_serialised_fixture_is_still_what_the_oracle_writes(lib, orc):
     assert np.array_equal(np.sort(values), np.arange(p["n"], dtype=np.uint64))
     info = M.load_info(blob)
     assert (info.n, info.nb, info.n_nodes) == (p["n"], 3, o.n_nodes)
+
+
+def test_mutated_headers_and_lengths_never_crash_the_decoder(lib):
+    """20,000 mutations of the golden blob (header words random or small,
+    payload words random, lengths cut or padded): the host decoder returns
+    OK or EINVAL every time and reads nothing outside the given length."""
+    from helpers import read_serialised_fixture
+    _, blob, _, _ = read_serialised_fixture()
+    w0 = np.frombuffer(blob, np.uint64).copy()
+    rng = np.random.default_rng(2212)
+    seen = {M.OK: 0, M.EINVAL: 0}
+    for it in range(20_000):
+        w = w0.copy()
+        kind = it % 4
+        if kind == 0:
+            w[rng.integers(1, 16)] = rng.integers(0, 2**63, dtype=np.uint64) >> np.uint64(rng.integers(0, 63))
+        elif kind == 1:
+            for i in rng.integers(1, 16, 3):
+                w[i] = rng.integers(0, 300)
+        elif kind == 2:
+            for i in rng.integers(16, len(w), 3):
+                w[i] = rng.integers(0, 2**63, dtype=np.uint64)
+        b = w.tobytes()
+        length = len(b) if kind != 3 else int(rng.integers(0, len(b) + 1))
+        buf = ctypes.create_string_buffer(b[:length], length)  # exactly `length` bytes
+        rc = lib.mphf_load_info(buf, length, ctypes.byref(M.Info()))
+        seen[rc] += 1
+    assert seen[M.OK] > 0 and seen[M.EINVAL] > 0
