@@ -273,8 +273,8 @@ def run_reference(args):
         return
     w = workload(args)
     keys = W.keys_for(w)
-    for _ in range(max(0, min(args.warmup, 1))):
-        cpu_baseline(w, keys, 2.0)
+    for _ in range(max(0, args.warmup)):  # untimed warm-up steps, about a second each
+        cpu_baseline(w, keys, 1.0)
     vals, secs = [], []
     for _ in range(args.steps):
         r = cpu_baseline(w, keys, args.cpu_seconds / max(1, args.steps))
