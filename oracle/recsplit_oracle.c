@@ -132,6 +132,8 @@ typedef struct {
     uint32_t lower2; /* largest lower-2 node: f2*f1*l        */
 } orc_shape;
 
+/* Fanouts and unit sizes of the tree for leaf size l (Section 2.2,
+ * "Splitting Trees"; reading R3, or R18 for the fanout-2 tree flag). */
 static orc_shape shape_of(uint32_t leaf_arg) {
     orc_shape sh;
     uint32_t leaf = leaf_arg & 0xFFu;
@@ -155,6 +157,8 @@ void orc_fanouts(uint32_t leaf, uint32_t *f1, uint32_t *f2) {
     *f2 = sh.f2;
 }
 
+/* Kind of the node of m keys (Section 2.2): none (m <= 1), leaf (m <= l),
+ * lower level 1 or 2, or fanout 2 above. */
 static int kind_of(const orc_shape *sh, uint32_t m) {
     if (m <= 1) return KIND_NONE;
     if (m <= sh->leaf) return KIND_LEAF;
@@ -190,7 +194,8 @@ uint32_t orc_parts(uint32_t leaf, uint32_t m, uint32_t *parts) {
     return parts_of(&sh, m, parts);
 }
 
-/* Number of stored nodes (nodes with at least two keys) in the tree of m. */
+/* Number of stored nodes (nodes with at least two keys) in the tree of m
+ * (Section 2.2: one stored value per node of the splitting tree). */
 static uint64_t count_nodes(const orc_shape *sh, uint32_t m) {
     if (m <= 1) return 0;
     if (m <= sh->leaf) return 1;
@@ -335,13 +340,16 @@ static int leaf_rotation(const uint64_t *lo, const uint64_t *hi, uint32_t m, uin
 /* ------------------------------------------------------------------------ */
 static double binom(uint32_t n, uint32_t k);
 
+/* The two cells of a key under seed s (Appendix C's two hash functions of
+ * a trial; reading R14: the two halves of one 64-bit hash). */
 static void sh_cells(uint64_t lo, uint64_t s, uint32_t m, uint32_t *c0, uint32_t *c1) {
     uint64_t h = orc_mix64(lo + orc_salt(0) + s);
     *c0 = (uint32_t)(h & 0xFFFFFFFFu) % m;
     *c1 = (uint32_t)(h >> 32) % m;
 }
 
-/* Union-find over the cells; orientable iff edges == cells in every component. */
+/* Union-find over the cells; orientable iff edges == cells in every
+ * component (Appendix C: the graph must be a pseudo-forest). */
 static int sh_orientable(const uint32_t *c0, const uint32_t *c1, uint32_t m) {
     uint32_t comp[ORC_MAX_LEAF], cells[ORC_MAX_LEAF], edges[ORC_MAX_LEAF];
     for (uint32_t v = 0; v < m; v++) {
@@ -413,7 +421,7 @@ static void sh_orientation(const uint64_t *lo, const uint32_t *c0, const uint32_
     }
 }
 
-/* Retrieval of one bit per key: solve row_i . Z = rhs_i over GF(2) by
+/* Retrieval of one bit per key (Appendix C; reading R16): solve row_i . Z = rhs_i over GF(2) by
  * Gauss-Jordan elimination, columns in increasing order, pivot row of a
  * column = the first remaining row with that bit.  Returns 1 and the
  * solution with zero non-pivot coordinates, or 0 if inconsistent. */
@@ -449,6 +457,7 @@ static int sh_solve(const uint32_t *row_in, const uint8_t *rhs_in, uint32_t m, u
     return 1;
 }
 
+/* A key's row of the retrieval system under seed s (reading R16, Appendix C). */
 static uint32_t sh_row(uint64_t lo, uint64_t s, uint32_t m) {
     uint64_t h = orc_mix64(lo + orc_salt(ORC_SH_RETRIEVAL_LEVEL) + s);
     return (uint32_t)(h & ((1ull << m) - 1));
@@ -477,7 +486,7 @@ static int leaf_shockhash(const uint64_t *lo, uint32_t m, uint64_t max_value, ui
 }
 
 /* Probability that m keys with two uniform cells each (out of m) admit a
- * bijection.  Counting labelled edge lists with ordered cell pairs: the
+ * bijection (Appendix C's success condition; used for tau, reading R17).  Counting labelled edge lists with ordered cell pairs: the
  * pairs (list, valid choice vector) number m! 2^m m^m (pick the bijection,
  * the bits, the free cell), and a list whose components are all unicyclic
  * has 2 choices per component.  With W(k) = k! 2^k k^k, the connected
@@ -504,7 +513,7 @@ double orc_shockhash_orient_prob(uint32_t m) {
 }
 
 /* Probability that m uniform random GF(2) rows of m bits give a solvable
- * system for a fixed nonzero right-hand side: sum over the rank r of
+ * system for a fixed nonzero right-hand side (retrieval, reading R17): sum over the rank r of
  * P(rank r) * (2^r - 1)/(2^m - 1), the column space being a uniform
  * r-dimensional subspace; P(rank r) = 2^-(m-r)^2 prod_{i<r}
  * (1 - 2^(i-m))^2 / (1 - 2^(i-r)). */
@@ -582,7 +591,8 @@ double orc_rotation_success_bound(uint32_t m) {
 /* Success probability of one brute-force leaf trial: m!/m^m. */
 double orc_plain_success(uint32_t m) { return prob_distinct(m, m); }
 
-/* Success probability of one split trial: multinomial m!/prod p_i! prod (p_i/m)^p_i. */
+/* Success probability of one split trial (Section 2.2, "Splitting Trees"):
+ * multinomial m!/prod p_i! prod (p_i/m)^p_i. */
 static double split_success(const orc_shape *sh, uint32_t m) {
     uint32_t parts[ORC_MAX_PARTS];
     uint32_t np = parts_of(sh, m, parts);
@@ -605,7 +615,9 @@ uint32_t orc_kiely_tau(double p) {
     return t < 0.0 ? 0u : (uint32_t)t;
 }
 
-/* Success probability per stored unit of the node of m keys.  A ShockHash
+/* Success probability per stored unit of the node of m keys, the p of the
+ * Golomb-Rice parameter (Section 2.2, "Representation"; reading R7; Appendix
+ * A's bound for rotation leaves).  A ShockHash
  * trial succeeds when the graph admits a bijection and the retrieval system
  * of its chosen bits is solvable (taken as independent events). */
 static double unit_success(const orc_shape *sh, int bij, uint32_t m) {
@@ -625,8 +637,8 @@ void orc_tau_table(uint32_t leaf, int bij, uint32_t max_m, uint8_t *tau) {
         tau[m] = m < 2 ? 0 : (uint8_t)orc_kiely_tau(unit_success(&sh, bij, m));
 }
 
-/* Fixed-part width of a node: tau bits of the value, plus the m retrieval
- * bits of a ShockHash leaf. */
+/* Fixed-part width of a node (Section 2.2, "Representation"): tau bits of
+ * the value, plus the m retrieval bits of a ShockHash leaf (reading R16). */
 static uint32_t fixed_width(const orc_shape *sh, int bij, const uint8_t *tau, uint32_t m) {
     uint32_t w = tau[m];
     if (bij == ORC_BIJ_SHOCKHASH && kind_of(sh, m) == KIND_LEAF) w += m;
@@ -648,6 +660,9 @@ static uint32_t floor_log2_u64(uint64_t x) {
     return r;
 }
 
+/* Elias-Fano sizes of k values ending at `last` (Section 2.1, "Elias-Fano";
+ * the two bucket sequences of Section 2.2, "Representation"; reading R9):
+ * L = floor(log2(last / k)) low bits each. */
 static ef_dims ef_dims_of(uint64_t k, uint64_t last) {
     ef_dims d;
     d.L = last >= k ? floor_log2_u64(last / k) : 0;
@@ -659,6 +674,8 @@ static ef_dims ef_dims_of(uint64_t k, uint64_t last) {
 static void set_bit(uint64_t *w, uint64_t i) { w[i >> 6] |= 1ull << (i & 63); }
 static int get_bit(const uint64_t *w, uint64_t i) { return (int)((w[i >> 6] >> (i & 63)) & 1); }
 
+/* Elias-Fano encoding of v[0..k) (Section 2.1, "Elias-Fano"): the low L
+ * bits of v[i] at i*L, a one at position (v[i] >> L) + i of the high part. */
 static void ef_encode(const uint64_t *v, uint64_t k, ef_dims d, uint64_t *low, uint64_t *high) {
     for (uint64_t i = 0; i < k; i++) {
         for (uint32_t j = 0; j < d.L; j++)
@@ -798,7 +815,8 @@ static int cmp_u64(const void *a, const void *b) {
 }
 
 /* Two keys of one bucket with the same lo word meet at every split and can
- * never be told apart by a leaf hash: the build refuses them. */
+ * never be told apart by a leaf hash: the build refuses them (reading R12;
+ * the paper assumes distinct keys, Section 1). */
 static int has_duplicate(const uint64_t *lo, uint32_t m, uint64_t *scratch) {
     memcpy(scratch, lo, (size_t)m * sizeof(uint64_t));
     qsort(scratch, m, sizeof(uint64_t), cmp_u64);
@@ -975,8 +993,9 @@ static int is_shock_leaf(const orc_mphf *h, const orc_shape *sh, uint32_t m) {
     return h->bij == ORC_BIJ_SHOCKHASH && kind_of(sh, m) == KIND_LEAF;
 }
 
-/* The Golomb-Rice coded number of a stored word: the seed of a ShockHash
- * leaf (its retrieval vector goes to the fixed part verbatim), else the word. */
+/* The Golomb-Rice coded number of a stored word (Section 2.2,
+ * "Representation"): the seed of a ShockHash leaf (its retrieval vector goes
+ * to the fixed part verbatim, reading R16), else the word. */
 static uint64_t coded_value(const orc_mphf *h, const orc_shape *sh, uint32_t m, uint64_t v) {
     return is_shock_leaf(h, sh, m) ? (v & ORC_SH_SEED_MASK) : v;
 }
@@ -992,7 +1011,8 @@ static uint64_t bucket_bits(const orc_mphf *h, const orc_shape *sh, const uint64
     return bits;
 }
 
-/* Node sizes of a bucket's tree in preorder. */
+/* Node sizes of a bucket's tree in preorder (Section 2.2: the values are
+ * stored in preorder). */
 static void preorder_sizes(const orc_shape *sh, uint32_t m, uint32_t *out, uint64_t *count) {
     if (m <= 1) return;
     out[(*count)++] = m;
@@ -1176,6 +1196,12 @@ static uint64_t node_value(const orc_mphf *h, uint64_t fixed_pos, uint32_t tau,
     return ((end - begin) << tau) | fixed;
 }
 
+/* The value of one key (Section 2.2, "Query"): its bucket, the bucket's key
+ * offset and code start from the Elias-Fano sequences, then from the root
+ * one decoded value and child per level, adding the sizes of the children to
+ * the left, down to the leaf: the key's position under the leaf's seed, plus
+ * r mod m for keys of B (Section 4), or the retrieved one of its two cells
+ * (Appendix C). */
 static uint64_t query_one(const orc_mphf *h, const orc_shape *sh, uint64_t hi, uint64_t lo) {
     uint64_t b = orc_bucket_of(hi, h->nb);
     const uint64_t *e = h->ef;
