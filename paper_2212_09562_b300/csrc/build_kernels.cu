@@ -166,7 +166,8 @@ void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64
 }
 
 // ---------------------------------------------------------------------------
-// Plan: nodes per bucket, oversized buckets, largest bucket, and a histogram
+// Plan (Section 2.2: the tree shape follows from the bucket size alone):
+// nodes per bucket, oversized buckets, largest bucket, and a histogram
 // of bucket sizes in descending order (size_hist[4096 - m]) for the work order.
 __global__ void k_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab,
                        uint64_t *node_cnt, uint32_t *status, uint32_t *max_m,
@@ -558,7 +559,9 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
     }
 }
 
-// Fanout-2 split: the number of keys hashed below `left` must be `left`.
+// Fanout-2 split (Section 2.2, "Splitting Trees": fanout 2 above the lower
+// levels; the whole tree in Appendix C): the number of keys hashed below
+// `left` must be `left`.
 // One seed per warp and round, the lanes sharing the node's keys, so a round
 // tests 16 seeds (512 threads): a fanout-2 split of m keys needs about
 // sqrt(pi m / 2) trials, far fewer than one seed per thread would test.
@@ -826,6 +829,7 @@ __device__ __forceinline__ uint32_t leaf_shock_bits(uint32_t c0, uint32_t c1, ui
     return beta;
 }
 
+// The retrieval vector of a ShockHash leaf (Appendix C; one bit per key).
 // Gauss-Jordan over GF(2), lane i < m holding row i and its bit: columns in
 // increasing order, the lowest remaining lane with the column's bit as pivot.
 // The reduced row echelon form is unique, so the solution with zero
@@ -947,6 +951,8 @@ __device__ __forceinline__ uint32_t select32(uint32_t x, uint32_t k) {
 // every cell, so every cell must be one of some key's two cells.  With 2m
 // uniform choices all m cells are covered with probability about
 // exp(-m e^-2) (4 % at m = 24), and the screen costs only the hashes.
+// ShockHash leaf (Appendix C): the smallest seed whose two cells per key
+// admit a bijection and whose retrieval system is solvable.
 // Passing seeds queue up in increasing order, one per lane; the queue gets
 // the union-find (one seed per lane) once it holds `batch` seeds, the round
 // would overflow it, or the seeds are exhausted.  The first queued seed
@@ -1040,6 +1046,10 @@ __device__ __forceinline__ bool block_has_duplicate(const uint64_t *lo, uint32_t
     return __syncthreads_or(dup);
 }
 
+// One inner node (Section 2.2, "Splitting Trees"; Section 5.3, "Splittings":
+// a thread block tries seeds, then regroups the node's keys): search its
+// smallest valid seed, store it in preorder, regroup its keys by child in
+// shared memory and push the children.
 template <int LEAF>
 __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, uint32_t off, uint32_t m,
                            uint32_t depth, uint32_t pidx, uint64_t nbase, uint32_t bucket_m,
@@ -1234,6 +1244,8 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
     }
 }
 
+// One bucket's whole splitting tree (Section 2.2): the inner nodes depth
+// first, then every leaf's bijection search, values written in preorder.
 template <int LEAF>
 __device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
                                BlockState &S) {
@@ -1293,6 +1305,9 @@ struct SmemLayout {
     }
 };
 
+// The persistent search (the brute-force searches of Section 2.2 in the
+// parallel form of Section 5.3): blocks take buckets from a device queue,
+// largest first, and run process_bucket on each.
 __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, const WorkItem *items,
                                                 uint32_t nitems, uint32_t *head, uint32_t cap) {
     extern __shared__ __align__(16) uint8_t dyn[];
@@ -1372,6 +1387,8 @@ __device__ __forceinline__ GrPiece gr_piece(uint64_t v, uint32_t m, uint32_t t, 
     return g;
 }
 
+// Golomb-Rice code length of each bucket (Section 2.1, "Golomb-Rice";
+// Section 2.2, "Representation"): fixed parts plus unary parts of its nodes.
 __global__ void k_gr_len(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                          uint64_t nb, const uint8_t *tau, uint32_t leaf, uint32_t bij,
                          uint64_t *bucket_bits) {
@@ -1406,6 +1423,8 @@ __device__ __forceinline__ void or_bits(uint64_t *w, uint64_t pos, uint64_t v, u
     if (sh + len > 64) atomicOr((unsigned long long *)&w[(pos >> 6) + 1], (unsigned long long)(v >> (64 - sh)));
 }
 
+// Golomb-Rice bits of each bucket (Section 2.2, "Representation"): all
+// fixed parts of its nodes in preorder, then all unary parts.
 __global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                            const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
                            const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
@@ -1477,7 +1496,8 @@ __global__ void k_popcount(const uint64_t *words, uint64_t n, uint64_t *out) {
     if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = 0;
 }
 
-// Stats: trials up to the stored value, and hash evaluations, per node kind.
+// Stats: trials up to the stored value, and hash evaluations, per node kind
+// (the smallest stored value is the number of failed trials, Section 5.1).
 __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes,
                         uint32_t leaf, uint32_t bij, uint32_t tree, unsigned long long *counters) {
     __shared__ unsigned long long acc[8];
@@ -1516,7 +1536,8 @@ void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint
     launch_exclusive_scan(dir, nwords + 1, tmp, st);
 }
 
-// Select directory of a bit vector: sel[j] = the word holding one number
+// For the select_1 queries of Section 2.2, "Query", on the Elias-Fano high
+// bits.  Select directory of a bit vector: sel[j] = the word holding one number
 // 64 j.  Word w holds the ones dir[w] .. dir[w + 1] - 1, so it writes every
 // multiple of 64 in that range (each entry exactly once).
 __global__ void k_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel) {

@@ -25,6 +25,8 @@
 
 namespace rs {
 
+// The remix of the node hash (Section 2.2, "a hash function modulo l"):
+// the SplitMix64 output function of Steele, Lea and Flood (OOPSLA 2014).
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z ^= z >> 30;
     z *= 0xBF58476D1CE4E5B9ull;
@@ -34,6 +36,9 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z;
 }
 
+// The master hash code of a key (Section 2.2, the initial hash; Section 6
+// uses random 128-bit codes): three Feistel rounds, invertible, so distinct
+// keys never share a fingerprint.
 __host__ __device__ __forceinline__ void fingerprint(uint64_t w0, uint64_t w1, uint64_t &hi,
                                                      uint64_t &lo) {
     uint64_t t1 = w1 ^ mix64(w0 + MPHF_GOLDEN);

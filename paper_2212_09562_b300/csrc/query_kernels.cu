@@ -108,6 +108,8 @@ __device__ __forceinline__ uint64_t node_value(const uint64_t *gr, uint64_t fixe
     return (u.value(gr, idx) << tau) | fixed;
 }
 
+// One thread per key (Section 2.2, "Query"; the walk is described at the
+// top of this file).
 // The walk reads every per-size constant from tables (remainder constants,
 // fanout-2 left parts, the unit divisors' magic numbers): computing them in
 // the kernel would cost 64-bit divisions at every level.
@@ -200,7 +202,8 @@ void launch_query(const QueryView &q, const void *keys, uint64_t n, uint64_t *ou
     note_launches(1);
 }
 
-// Bijection check: every value below n and taken once.
+// Bijection check (Section 1: h maps the n keys onto [0, n) one to one):
+// every value below n and taken once.
 __global__ void k_mark(const uint64_t *vals, uint64_t n, uint32_t *bitmap, unsigned long long *bad) {
     unsigned long long local = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
