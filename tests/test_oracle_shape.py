@@ -4,6 +4,7 @@ The lower aggregation fanouts are max(2, ceil(0.35 l + 0.55)) and
 max(2, ceil(0.21 l + 0.9)); the upper levels use fanout 2.  Exact rational
 arithmetic below gives the ceilings without floating-point doubt.
 """
+import os
 from fractions import Fraction
 from math import ceil
 
@@ -45,6 +46,9 @@ def test_parts_partition_every_node(orc, leaf):
             assert len(p) == 2
             left, right = p
             assert left % lower2 == 0 and left >= m // 2 and right >= 1
+            # the SMALLEST such multiple (reading of the fanout-2 left size):
+            # one unit less would fall below floor(m/2)
+            assert left - lower2 < m // 2
 
 
 @pytest.mark.parametrize("leaf", [4, 8, 12, 16])
@@ -81,3 +85,14 @@ def test_node_counts(orc):
 def test_salts_distinct(orc):
     salts = [orc.salt(l) for l in range(40)]
     assert len(set(salts)) == 40
+
+
+def test_salts_are_the_published_splitmix64_outputs(orc):
+    """salt(L) = mix64((L + 1) G) is output L of SplitMix64 started from state
+    0 (Steele, Lea and Flood, OOPSLA 2014), whose first outputs are published.
+    An off-by-one in the level index (mix64(L G)) or a wrong increment fails."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "splitmix64_seed0.txt")) as f:
+        golden = [int(line, 16) for line in f if line.strip() and not line.startswith("#")]
+    assert len(golden) == 4
+    assert [orc.salt(level) for level in range(4)] == golden
