@@ -32,10 +32,18 @@ from paper_2212_09562_b300 import workloads as W  # noqa: E402
 
 METRIC = "MPHF build keys/s + seed trials/s vs IMAD peak (ℓ=16,b=2000), batched vs plain"
 WORKLOAD = "rot_l16"
-# Integer instructions that one key-hash evaluation needs at least on 32-bit
-# integer lanes: 64-bit add (2), three 64-bit xor-shifts (4 each), two
-# 64x64->64 multiplies (3 each), exact 64-bit mod m by a constant (3 wide
-# multiply-adds + 3 for the final 32-bit remainder), child counter update (3).
+# Integer-multiply (IMAD pipe) work of one key-hash evaluation at a full
+# lower-level node, by instruction form: the two 64 x 64 -> 64-bit multiplies
+# of the SplitMix64 remix on 32-bit lanes (each one 32 x 32 -> 64 wide
+# multiply-add and two 32-bit multiply-adds), the fold of h to 32 bits
+# congruent mod m (one wide multiply-add), and the remainder by the constant
+# node size (one multiply-high, one multiply-subtract).  Each form is weighted
+# by its issue cost relative to mad.lo.u32, measured in the same run by the
+# integer microbenchmark (peaks/int_peaks.cu).
+IMAD_FORMS_PER_EVAL = {"mad.wide.u32": 3, "mad.lo.u32": 5, "mad.hi.u32": 1}
+# All integer instructions one evaluation needs at least on 32-bit lanes:
+# 64-bit add (2), three 64-bit xor-shifts (4 each), two 64 x 64-bit multiplies
+# (3 each), exact remainder (3 multiply forms + 3 shift/add/carry), counter (3).
 OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # DRAM bytes the search kernel moves per key (lo word and rotation bit read
 # once per bucket), from dram__bytes_read.sum + dram__bytes_write.sum of one
@@ -43,8 +51,49 @@ OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # traffic of a launch grows with its key count.
 SEARCH_DRAM_BYTES_PER_KEY = 6_386_432 / 600_000
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
-SMS, SMSP_PER_SM, LANES, SM_MAX_MHZ = 148, 4, 32, 2032.0
-PEAK_INT_OPS = SMS * SMSP_PER_SM * LANES * SM_MAX_MHZ * 1e6  # issue-slot bound, lane-ops/s
+
+
+def measured_int_peaks() -> dict:
+    """Integer issue rates of this GPU measured now (full grid, CUDA events):
+    mad.lo.u32, mad.wide.u32, mad.hi.u32 and the mixed IMAD + LOP3 issue rate."""
+    from paper_2212_09562_b300 import intpeaks as P
+    return {k: P.measure(k, reps=3, target_ms=20.0) for k in ("imad", "imad_wide", "imad_hi",
+                                                              "imad+lop3", "mul64")}
+
+
+def search_roofline(peaks: dict, evals_per_launch: float, launch_ms: float, bench_mhz,
+                    traffic) -> dict:
+    """Roofline of the search kernel against the measured integer-multiply peak.
+    achieved = IMAD-equivalent operations per launch / launch time; the peak is
+    mad.lo.u32 over a full grid, scaled to the SM clock of the timed region."""
+    imad = peaks["imad"]
+    scale = (bench_mhz / imad["sm_mhz"]) if (bench_mhz and imad["sm_mhz"]) else 1.0
+    peak = imad["per_s"] * scale
+    w = {"mad.lo.u32": 1.0, "mad.wide.u32": imad["per_s"] / peaks["imad_wide"]["per_s"],
+         "mad.hi.u32": imad["per_s"] / peaks["imad_hi"]["per_s"]}
+    eq = sum(IMAD_FORMS_PER_EVAL[k] * w[k] for k in IMAD_FORMS_PER_EVAL)
+    raw = sum(IMAD_FORMS_PER_EVAL.values())
+    evals_per_s = evals_per_launch / (launch_ms / 1e3)
+    achieved = evals_per_s * eq
+    issue = peaks["imad+lop3"]["per_s"] * scale
+    return {"bound": "alu", "kernel": "k_search", "unit": "T IMAD-equivalents/s",
+            "achieved": achieved / 1e12, "peak": peak / 1e12, "frac": achieved / peak,
+            "peak_basis": (f"measured in this run (of measured): mad.lo.u32 over a full grid, "
+                           f"{imad['per_s'] / 1e12:.3f} T/s at {imad['sm_mhz']:.0f} MHz, "
+                           f"scaled to the timed region's {bench_mhz} MHz"),
+            "imad_forms_per_eval": IMAD_FORMS_PER_EVAL,
+            "measured_weights": {k: round(v, 3) for k, v in w.items()},
+            "imad_equivalents_per_eval": eq,
+            "mul64_check": {"predicted_equiv": w["mad.wide.u32"] + 2,
+                            "measured_equiv": imad["per_s"] / peaks["mul64"]["per_s"]},
+            "frac_unweighted": evals_per_s * raw / peak,
+            "issue": {"ops_per_eval": OPS_PER_EVAL,
+                      "peak_T_per_s": issue / 1e12,
+                      "basis": "measured mixed mad.lo.u32 + lop3.b32 issue rate (of measured)",
+                      "frac": evals_per_s * OPS_PER_EVAL / issue},
+            "evals_per_launch": evals_per_launch, "launch_ms": launch_ms,
+            "traffic": traffic,
+            "traffic_basis": "ncu DRAM bytes of k_search at 6e5 keys of rot_l16, scaled by n"}
 
 
 def parse():
@@ -58,7 +107,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the key count (profiling runs)")
-    ap.add_argument("--mode", choices=["build", "serve", "batch"], default="build")
+    ap.add_argument("--mode", choices=["build", "serve", "batch", "peaks"], default="build")
     ap.add_argument("--requests", type=int, default=24, help="serve mode: requests per run")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: Poisson arrivals per second")
     ap.add_argument("--batch-builds", type=int, default=128,
@@ -153,6 +202,14 @@ def cpu_baseline(w, keys, budget_s: float) -> dict:
             "seconds": dt, "trials_per_s": trials / dt}
 
 
+def same_function(a, b) -> bool:
+    """Word-for-word equality of two built functions: node values, offsets,
+    Golomb-Rice and Elias-Fano words."""
+    x, y = a.host_arrays(), b.host_arrays()
+    return all(np.array_equal(x[k], y[k]) for k in ("values", "node_off", "cum_keys", "bit_pos",
+                                                     "gr", "ef"))
+
+
 def batch_vs_plain(M, torch, count: int, hi_exp: float = 5.0) -> dict:
     """The same independent builds (batch workload distribution, sizes
     10^3..10^hi_exp) through one batched call and through one call per build."""
@@ -171,9 +228,7 @@ def batch_vs_plain(M, torch, count: int, hi_exp: float = 5.0) -> dict:
     plain = [M.MPHF.build(k, l, 2000, True) for k, l in zip(keys, leaves)]
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
-    identical = all(np.array_equal(a.host_arrays()["values"], b.host_arrays()["values"]) and
-                    np.array_equal(a.host_arrays()["gr"], b.host_arrays()["gr"])
-                    for a, b in zip(batched, plain))
+    identical = all(same_function(a, b) for a, b in zip(batched, plain))
     for g in batched + plain:
         g.close()
     return {"builds": count, "keys": total,
@@ -264,6 +319,26 @@ def run_batch(args):
                       "sizes": r["sizes"]},
            "plain_keys_per_s": r["plain_keys_per_s"], "batched_over_plain": r["batched_over_plain"],
            "identical": r["identical"], "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
+def run_peaks(args):
+    """Integer issue rates of this GPU, one instruction class at a time
+    (paper_2212_09562_b300/peaks/int_peaks.cu), with the SM clock each ran at."""
+    import torch
+    from paper_2212_09562_b300 import intpeaks as P
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    rows = {k: P.measure(k, reps=5, target_ms=40.0) for k in P.KINDS}
+    clocks = sampler.stop()
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    for r in rows.values():
+        # thread-level operations per SM per clock at the clock the kernel ran at
+        r["per_sm_per_clock"] = r["per_s"] / (sms * r["sm_mhz"] * 1e6) if r["sm_mhz"] else None
+    out = {"metric": "integer issue rates (thread ops per SM per clock)", "mode": "peaks",
+           "device": props.name, "sms": sms, "rates": rows, "clocks": clocks}
     print(json.dumps(out), flush=True)
 
 
@@ -363,6 +438,7 @@ def run_ours(args):
 
     for i in range(args.warmup):
         M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation, tree=w.tree).close()
+    peaks = measured_int_peaks()  # before the timed region, on this GPU
     sampler = ClockSampler(local)
     sampler.start()
     step_ms, search_ms, evals, trials = [], [], 0, 0
@@ -415,15 +491,8 @@ def run_ours(args):
         return
     mean_search = statistics.mean(search_ms)
     evals_per_build = evals / args.steps
-    ops = evals_per_build * OPS_PER_EVAL
-    achieved = ops / (mean_search / 1000.0)
-    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": PEAK_INT_OPS / 1e12,
-            "unit": "Tintops/s", "frac": achieved / PEAK_INT_OPS,
-            "traffic": (SEARCH_DRAM_BYTES_PER_KEY * w.n if w.name.startswith("rot_l16") else None),
-            "traffic_basis": "ncu DRAM bytes of k_search at 6e5 keys of rot_l16, scaled by n",
-            "kernel": "k_search", "ops_per_eval": OPS_PER_EVAL,
-            "evals_per_launch": evals_per_build, "launch_ms": mean_search,
-            "peak_basis": "148 SMs x 4 SMSP x 32 lanes x 2032 MHz (integer issue slots)"}
+    roof = search_roofline(peaks, evals_per_build, mean_search, clocks.get("sm_mhz"),
+                           SEARCH_DRAM_BYTES_PER_KEY * w.n if w.name.startswith("rot_l16") else None)
     out = {"metric": METRIC, "value": keys_per_s, "unit": "keys/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
@@ -454,6 +523,8 @@ def main():
         run_serve(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "peaks":
+        run_peaks(args)
     else:
         run_ours(args)
 

@@ -17,6 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmphf.so")
+PEAKS_SRC = os.path.join(HERE, "peaks", "int_peaks.cu")
+PEAKS_LIB = os.path.join(HERE, "libintpeaks.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -32,6 +34,20 @@ def _stale() -> bool:
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
     deps.append(os.path.join(INCLUDE, "mphf.h"))
     return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build_peaks(force: bool = False, verbose: bool = False) -> str:
+    """Compiles the integer issue-rate microbenchmark (libintpeaks.so, measurement only)."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-Wall,-Wextra",
+           "-shared", PEAKS_SRC, "-o", tmp]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    subprocess.check_call(cmd)
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
@@ -53,3 +69,4 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 if __name__ == "__main__":
     extra = [a for a in sys.argv[1:] if a.startswith("-X") or a.startswith("--ptxas")]
     build(force="--force" in sys.argv, verbose=True, extra=extra)
+    build_peaks(force="--force" in sys.argv, verbose=True)

@@ -13,6 +13,9 @@
 // device race on it and must be serialised (one stream, or wait for the
 // previous call).  The first call on a device looks up the scratch address
 // with cudaGetSymbolAddress; make that first call before any stream capture.
+// The address is kept for the life of the process: a cudaDeviceReset (or any
+// other teardown of the device's primary context) makes it stale, so the
+// entry point must not be called on a device after it was reset.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

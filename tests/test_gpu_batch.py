@@ -4,6 +4,8 @@ launch must equal the same builds made one by one, and the oracle.
 A failing member (duplicate keys, bad parameters) fails alone; the others
 are unaffected.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -93,3 +95,19 @@ def test_batch_workload_sample(torch, orc):
             if x.leaf < 16:
                 o = orc.build_mphf(k, x.leaf, 2000, True, threads=8)
                 assert np.array_equal(batch[i].host_arrays()["values"], o.values)
+
+
+def test_batch_leaf16_members_match_the_oracle(torch, orc):
+    """Members with l = 16 (the dominant cost of the batch workload) built in
+    one batch with smaller ones, each equal to its oracle build word for word."""
+    specs = [(20_000, 16), (1_500, 8), (30_000, 16), (7_000, 12), (3_000, 16)]
+    keys = [W.distinct_u64(n, 1700 + i) for i, (n, _) in enumerate(specs)]
+    dkeys = [dev(torch, k) for k in keys]
+    batch = M.build_batch(dkeys, [l for _, l in specs], bucket_size=2000)
+    for (n, l), k, dk, g in zip(specs, keys, dkeys, batch):
+        o = orc.build_mphf(k, l, 2000, True, threads=os.cpu_count() or 4)
+        a = g.host_arrays()
+        for name, ref in (("values", o.values), ("node_off", o.node_off), ("cum_keys", o.cum_keys),
+                          ("bit_pos", o.bit_pos), ("gr", o.gr), ("ef", o.ef)):
+            assert np.array_equal(a[name], ref), (n, l, name)
+        assert g.verify(dk) == 0

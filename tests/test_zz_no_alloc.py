@@ -68,3 +68,35 @@ def test_static_verify_rejects_more_keys_than_its_scratch(torch):
     rc, bad = _check(M.lib().mphf_verify_static, h, dkeys, n, torch)
     assert rc == M.EINVAL and bad == 0
     assert h.verify(dkeys) == 0
+
+
+def test_static_verify_makes_no_allocator_call(torch):
+    """With h built through counting allocator hooks, mphf_verify takes its
+    scratch from those hooks on every call, while mphf_verify_static asks for
+    nothing: its scratch is the library's fixed device array."""
+    from test_gpu_allocator import CountingAllocator
+    n = 300_000
+    keys = W.distinct_u64(n, 909)
+    dkeys = torch.from_numpy(keys.view(np.int64)).cuda()
+    A = CountingAllocator(torch)
+    p = A.params(12, 1000, M.ROTATION, M.TREE_RECSPLIT, 8)
+    hh = ctypes.c_void_p()
+    L = M.lib()
+    assert L.mphf_build_ex(ctypes.c_void_p(dkeys.data_ptr()), n, ctypes.byref(p), _stream(torch),
+                           ctypes.byref(hh)) == M.OK
+    h = M.MPHF(hh.value)
+    try:
+        before = A.calls
+        rc_a, bad_a = _check(L.mphf_verify, h, dkeys, n, torch)
+        assert rc_a == M.OK and bad_a == 0 and A.calls > before
+        torch.cuda.synchronize()
+        mem0 = torch.cuda.memory_allocated()
+        for _ in range(2):
+            before = A.calls
+            rc_b, bad_b = _check(L.mphf_verify_static, h, dkeys, n, torch)
+            assert rc_b == M.OK and bad_b == 0
+            assert A.calls == before
+        assert torch.cuda.memory_allocated() == mem0
+    finally:
+        h.close()
+    assert A.live == 0
