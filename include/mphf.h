@@ -181,6 +181,63 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *param
 int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *params,
                     void *stream, mphf_t **out);
 
+/* ---------------------------------------------------------------------------
+ * One function built on several GPUs (Section 5.2, "Multi-Threading": each
+ * worker builds a consecutive range of buckets; the local Golomb-Rice
+ * sequences and bucket offsets are concatenated).  Rank r of `world` owns
+ * buckets [floor(r nb / world), floor((r + 1) nb / world)) of the function
+ * over n_total keys, nb = ceil(n_total / bucket_size).  The steps:
+ *   1. mphf_shard_route on each rank's own keys: keys grouped by owner rank;
+ *   2. an exchange of keys between ranks (the caller's collective, e.g. an
+ *      all-to-all) so that each rank holds exactly its buckets' keys;
+ *   3. mphf_build_shard on each rank: the rank's buckets, searched and packed;
+ *   4. mphf_shard_pack, and a gather of every rank's pack (the caller's
+ *      collective) to wherever the whole function is wanted;
+ *   5. mphf_shard_concat: the whole function, word for word the one that
+ *      mphf_build_ex makes from all n_total keys on one device. */
+#define MPHF_MAX_SHARDS 1024u
+
+/* Groups the n keys at d_keys (device, key_bytes each, 8-byte aligned) by
+ * the rank that owns their bucket: d_out (n keys, device) receives rank 0's
+ * keys, then rank 1's, ...; h_counts[r] (host, world entries) the number of
+ * keys for rank r.  The order within a rank's keys is unspecified (builds do
+ * not depend on it).  Errors: MPHF_EINVAL for bad sizes or pointers
+ * (n <= n_total < 2^32, world <= MPHF_MAX_SHARDS), MPHF_ENOMEM, MPHF_ECUDA.
+ * Synchronises the stream. */
+int mphf_shard_route(const void *d_keys, uint64_t n, uint32_t key_bytes, uint64_t n_total,
+                     uint32_t bucket_size, uint32_t world, void *d_out, uint64_t *h_counts,
+                     void *stream);
+
+/* Builds rank `rank`'s buckets of the function over n_total keys from the n
+ * keys at d_keys, which must be exactly the keys of those buckets (any other
+ * key gives MPHF_EINVAL).  params as for mphf_build_ex.  The shard holds the
+ * range's node values, local offsets (starting at 0) and its own Golomb-Rice
+ * sequence (mphf_get_values, mphf_get_bits, mphf_get_stats work); it cannot
+ * be queried, verified or serialised (MPHF_EINVAL).  Free with mphf_free. */
+int mphf_build_shard(const void *d_keys, uint64_t n, uint64_t n_total,
+                     const mphf_build_params *params, uint32_t rank, uint32_t world,
+                     void *stream, mphf_t **out);
+
+/* Writes a shard into the device buffer d_buf (8-byte aligned) of *len bytes:
+ * 24 header words (magic "RMPFSHD1", n, the range's bucket count, its first
+ * bucket, n_total, node count, Golomb-Rice bits, leaf_size | tree_shape << 16,
+ * bucket_size, key_bytes, leaf_bijection, largest bucket, 4 zero words, the
+ * 4 trial and 4 evaluation counters of mphf_stats), then cum_keys, node_off,
+ * bit_pos (nb + 1 words each), the node values and the Golomb-Rice words.
+ * With d_buf NULL, *len receives the size needed.  MPHF_EINVAL for a handle
+ * that is not a shard or a buffer too small.  Synchronises the stream. */
+int mphf_shard_pack(const mphf_t *shard, void *d_buf, size_t *len, void *stream);
+
+/* Builds the whole function on the current device from the packs of ranks
+ * 0..count-1 (device memory, lens[i] bytes each, in rank order): node values
+ * and offsets concatenated, Golomb-Rice sequences joined at their bit
+ * offsets, the Elias-Fano sequences and query directories built once.  The
+ * statistics are the sums of the shards'.  MPHF_EINVAL unless the packs are
+ * the ranks of one function in order.  Device memory from allocator (NULL:
+ * cudaMallocAsync).  Synchronises the stream. */
+int mphf_shard_concat(const void *const *d_parts, const size_t *lens, uint32_t count,
+                      const mphf_allocator *allocator, void *stream, mphf_t **out);
+
 /* Evaluates h on n keys (Section 2.2, "Query"; Section 4 for the rotation
  * of the keys in B; Appendix C for the retrieved cell of a ShockHash leaf).
  * d_out[i] = h(key i) in [0, n_built) for keys of the built set; d_out holds
@@ -205,7 +262,9 @@ int mphf_verify(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad
  *   n <= MPHF_VERIFY_STATIC_MAX_KEYS, else MPHF_EINVAL (nothing is run).
  *   Every call shares the scratch: calls whose work overlaps on the device
  *   race and must be serialised.  The first call on a device looks up the
- *   scratch address; make it before any stream capture.  Synchronises. */
+ *   scratch address; make it before any stream capture.  The address is
+ *   kept until the process exits: do not call this on a device after a
+ *   cudaDeviceReset of it.  Synchronises. */
 #define MPHF_VERIFY_STATIC_MAX_KEYS 1048576u
 int mphf_verify_static(const mphf_t *h, const void *d_keys, uint64_t n, uint64_t *n_bad,
                        void *stream);

@@ -90,6 +90,9 @@ def lib() -> ctypes.CDLL:
             L.orc_build.argtypes = [p, u64, u32, u32, u32, ctypes.c_int, u64, ctypes.c_int,
                                     ctypes.POINTER(p)]
             L.orc_build_sample.restype = ctypes.c_int
+            L.orc_build_range.restype = ctypes.c_int
+            L.orc_build_range.argtypes = [p, u64, u32, u64, u32, u32, ctypes.c_int, u64, ctypes.c_int,
+                                          u64, u64, p]
             L.orc_build_sample.argtypes = [p, u64, u32, u32, u32, ctypes.c_int, u64, ctypes.c_int,
                                            p, u64, p, p, p]
             L.orc_free.argtypes = [p]
@@ -263,6 +266,22 @@ def build_mphf(keys: np.ndarray, leaf: int, bucket: int, rotation=True,
     h = ctypes.c_void_p()
     rc = lib().orc_build(_ptr(k), k.shape[0], kb, _leaf(leaf, tree), bucket, bij(rotation), max_value,
                          threads, ctypes.byref(h))
+    if rc != OK:
+        raise OracleError(rc)
+    return OracleMPHF(h.value, kb)
+
+
+def build_range(keys: np.ndarray, n_total: int, leaf: int, bucket: int, rotation, b_lo: int,
+                b_hi: int, max_value: int = DEFAULT_MAX_VALUE, threads: int = 1,
+                tree: int = TREE_RECSPLIT) -> OracleMPHF:
+    """Buckets [b_lo, b_hi) of the function over n_total keys, from the keys of
+    exactly those buckets (Section 5.2's consecutive bucket range).  Its
+    cum_keys, node_off and bit_pos are local to the range (start at 0); gr is
+    the range's own Golomb-Rice sequence.  Not queryable."""
+    k, kb = _key_bytes(keys)
+    h = ctypes.c_void_p()
+    rc = lib().orc_build_range(_ptr(k), k.shape[0], kb, n_total, _leaf(leaf, tree), bucket,
+                               bij(rotation), max_value, threads, b_lo, b_hi, ctypes.byref(h))
     if rc != OK:
         raise OracleError(rc)
     return OracleMPHF(h.value, kb)

@@ -1022,18 +1022,31 @@ static void preorder_sizes(const orc_shape *sh, uint32_t m, uint32_t *out, uint6
     for (uint32_t i = 0; i < np; i++) preorder_sizes(sh, parts[i], out, count);
 }
 
-/* Full build.  Returns ORC_OK and a new function in *out, or an error. */
-int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf,
-              uint32_t bucket_size, int bij, uint64_t max_value, int threads,
-              orc_mphf **out) {
+/* Builds buckets [b_lo, b_hi) of the function over n_total keys from the n
+ * keys that fall into exactly those buckets (Section 5.2: a thread that
+ * takes a consecutive range of buckets produces that range's node values,
+ * a local Golomb-Rice sequence and local bucket offsets; the ranges'
+ * sequences concatenated in bucket order are the function's).  The arrays
+ * of the result are local to the range: cum_keys, node_off and bit_pos
+ * start at 0.  A key whose bucket lies outside the range gives ORC_EINVAL.
+ * A full build is the range [0, nb) of its own keys. */
+static int build_range(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint64_t n_total,
+                       uint32_t leaf, uint32_t bucket_size, int bij, uint64_t max_value,
+                       int threads, uint64_t b_lo, uint64_t b_hi, orc_mphf **out) {
     *out = NULL;
-    int rc = check_params(n, key_bytes, leaf, bucket_size, bij);
+    int rc = check_params(n_total, key_bytes, leaf, bucket_size, bij);
     if (rc) return rc;
+    const uint64_t nb_total = (n_total + bucket_size - 1) / bucket_size;
+    if (n > n_total || b_lo > b_hi || b_hi > nb_total) return ORC_EINVAL;
     orc_shape sh = shape_of(leaf);
-    uint64_t nb = (n + bucket_size - 1) / bucket_size;
+    const uint64_t nb = b_hi - b_lo;
     grouped g;
-    rc = group_keys(keys, n, key_bytes, nb, &g);
+    rc = group_keys(keys, n, key_bytes, nb_total, &g);
     if (rc) return rc;
+    if (g.cum[b_lo] != 0 || g.cum[b_hi] != n) { /* some key belongs to another range */
+        free_grouped(&g);
+        return ORC_EINVAL;
+    }
     orc_mphf *h = calloc(1, sizeof(orc_mphf));
     if (!h) { free_grouped(&g); return ORC_ENOMEM; }
     h->n = n; h->nb = nb; h->leaf = leaf; h->bucket_size = bucket_size;
@@ -1052,13 +1065,13 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
     }
     orc_tau_table(leaf, bij, ORC_MAX_BUCKET, h->tau);
     fill_subtree_tables(&sh, bij, h->tau, ORC_MAX_BUCKET, h->nodes_tab, h->fixed_tab);
-    memcpy(h->cum_keys, g.cum, (nb + 1) * sizeof(uint64_t));
+    memcpy(h->cum_keys, g.cum + b_lo, (nb + 1) * sizeof(uint64_t));
     h->node_off[0] = 0;
     for (uint64_t b = 0; b < nb; b++) {
-        uint64_t m = g.cum[b + 1] - g.cum[b];
+        uint64_t m = h->cum_keys[b + 1] - h->cum_keys[b];
         if (m > ORC_MAX_BUCKET) { rc = ORC_EBUCKET; goto fail; }
         h->node_off[b + 1] = h->node_off[b] + count_nodes(&sh, (uint32_t)m);
-        list[b] = b;
+        list[b] = b_lo + b;
     }
     h->values = calloc(h->node_off[nb] ? h->node_off[nb] : 1, sizeof(uint64_t));
     if (!h->values) { rc = ORC_ENOMEM; goto fail; }
@@ -1072,7 +1085,7 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
         if (!sizes) { rc = ORC_ENOMEM; goto fail; }
         h->bit_pos[0] = 0;
         for (uint64_t b = 0; b < nb; b++) {
-            uint32_t m = (uint32_t)(g.cum[b + 1] - g.cum[b]);
+            uint32_t m = (uint32_t)(h->cum_keys[b + 1] - h->cum_keys[b]);
             uint64_t cnt = 0;
             preorder_sizes(&sh, m, sizes, &cnt);
             h->bit_pos[b + 1] = h->bit_pos[b] + bucket_bits(h, &sh, h->values + h->node_off[b], sizes, cnt);
@@ -1082,7 +1095,7 @@ int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf
         h->gr = calloc(h->gr_words ? h->gr_words : 1, sizeof(uint64_t));
         if (!h->gr) { free(sizes); rc = ORC_ENOMEM; goto fail; }
         for (uint64_t b = 0; b < nb; b++) {
-            uint32_t m = (uint32_t)(g.cum[b + 1] - g.cum[b]);
+            uint32_t m = (uint32_t)(h->cum_keys[b + 1] - h->cum_keys[b]);
             uint64_t cnt = 0;
             preorder_sizes(&sh, m, sizes, &cnt);
             const uint64_t *vals = h->values + h->node_off[b];
@@ -1132,6 +1145,26 @@ fail:
     free_grouped(&g);
     orc_free(h);
     return rc;
+}
+
+/* Full build.  Returns ORC_OK and a new function in *out, or an error. */
+int orc_build(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint32_t leaf,
+              uint32_t bucket_size, int bij, uint64_t max_value, int threads,
+              orc_mphf **out) {
+    *out = NULL;
+    if (bucket_size < 1) return ORC_EINVAL;
+    const uint64_t nb = (n + bucket_size - 1) / bucket_size;
+    return build_range(keys, n, key_bytes, n, leaf, bucket_size, bij, max_value, threads, 0, nb,
+                       out);
+}
+
+/* One consecutive bucket range of the function over n_total keys (see
+ * build_range); the result's query is not defined. */
+int orc_build_range(const uint8_t *keys, uint64_t n, uint32_t key_bytes, uint64_t n_total,
+                    uint32_t leaf, uint32_t bucket_size, int bij, uint64_t max_value, int threads,
+                    uint64_t b_lo, uint64_t b_hi, orc_mphf **out) {
+    return build_range(keys, n, key_bytes, n_total, leaf, bucket_size, bij, max_value, threads,
+                       b_lo, b_hi, out);
 }
 
 /* Builds only the listed buckets of the full key set and writes their node

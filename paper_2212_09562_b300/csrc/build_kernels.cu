@@ -52,21 +52,34 @@ static uint32_t grid_for(uint64_t n, uint32_t threads, uint32_t cap = 148u * 32u
 
 // ---------------------------------------------------------------------------
 // Fingerprint + bucket histogram.
-__global__ void k_fp_hist(const void *keys, uint64_t n, uint32_t kb, uint64_t nb,
-                          unsigned long long *counts) {
+// A key's bucket is mulhi64(hi, R.nb_hash) - R.b_lo (R.b_lo = 0 and nb_hash =
+// nb for a whole function; a shard holds the consecutive range [b_lo, b_lo +
+// nb) of a function with nb_hash buckets, Section 5.2).  A key outside the
+// range sets ST_RANGE and is not counted.
+__device__ __forceinline__ bool local_bucket(const BucketRange &R, uint64_t hi, uint64_t nb,
+                                             uint32_t *status, uint64_t &b) {
+    b = mulhi64(hi, R.nb_hash) - R.b_lo;  // wraps to a huge value below b_lo
+    if (b < nb) return true;
+    atomicOr(status, ST_RANGE);
+    return false;
+}
+
+__global__ void k_fp_hist(const void *keys, uint64_t n, uint32_t kb, uint64_t nb, BucketRange R,
+                          unsigned long long *counts, uint32_t *status) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t w0, w1, hi, lo;
+        uint64_t w0, w1, hi, lo, b;
         load_key(keys, i, kb, w0, w1);
         fingerprint(w0, w1, hi, lo);
-        atomicAdd(&counts[mulhi64(hi, nb)], 1ull);
+        if (local_bucket(R, hi, nb, status, b)) atomicAdd(&counts[b], 1ull);
     }
 }
 
-void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint64_t *counts,
-                    cudaStream_t st) {
+void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                    const BucketRange &R, uint64_t *counts, uint32_t *status, cudaStream_t st) {
     if (n == 0) return;
-    k_fp_hist<<<grid_for(n, 256), 256, 0, st>>>(keys, n, key_bytes, nb, (unsigned long long *)counts);
+    k_fp_hist<<<grid_for(n, 256), 256, 0, st>>>(keys, n, key_bytes, nb, R, (unsigned long long *)counts,
+                                                status);
     note_launches(1);
 }
 
@@ -80,17 +93,18 @@ void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 // from one per key to one per bucket and block.
 constexpr uint32_t kSmemBuckets = 8192;
 
-__global__ void k_fp_hist_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb,
-                              uint64_t chunk, unsigned long long *counts, uint32_t *blk) {
+__global__ void k_fp_hist_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb, BucketRange R,
+                              uint64_t chunk, unsigned long long *counts, uint32_t *blk,
+                              uint32_t *status) {
     extern __shared__ uint32_t hist[];
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const uint64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
     for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        uint64_t w0, w1, hi, lo;
+        uint64_t w0, w1, hi, lo, b;
         load_key(keys, i, kb, w0, w1);
         fingerprint(w0, w1, hi, lo);
-        atomicAdd(&hist[mulhi64(hi, nb)], 1u);
+        if (local_bucket(R, hi, nb, status, b)) atomicAdd(&hist[b], 1u);
     }
     __syncthreads();
     uint32_t *row = blk + (uint64_t)blockIdx.x * nb;
@@ -124,18 +138,20 @@ __global__ void k_block_offsets(uint32_t *blk, uint32_t G, uint32_t nb, const ui
     }
 }
 
-__global__ void k_scatter_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb, uint64_t chunk,
-                              const uint32_t *blk, uint64_t *lo_out, uint8_t *bb_out) {
+__global__ void k_scatter_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb, BucketRange R,
+                              uint64_t chunk, const uint32_t *blk, uint64_t *lo_out, uint8_t *bb_out,
+                              uint32_t *status) {
     extern __shared__ uint32_t cursor[];
     const uint32_t *row = blk + (uint64_t)blockIdx.x * nb;
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cursor[b] = row[b];
     __syncthreads();
     const uint64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
     for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        uint64_t w0, w1, hi, lo;
+        uint64_t w0, w1, hi, lo, b;
         load_key(keys, i, kb, w0, w1);
         fingerprint(w0, w1, hi, lo);
-        const uint32_t p = atomicAdd(&cursor[mulhi64(hi, nb)], 1u);
+        if (!local_bucket(R, hi, nb, status, b)) continue;
+        const uint32_t p = atomicAdd(&cursor[b], 1u);
         lo_out[p] = lo;
         bb_out[p] = (uint8_t)(hi & 1);
     }
@@ -148,20 +164,22 @@ uint32_t sort_blocks(uint64_t n, uint64_t nb) {
 }
 
 void launch_fp_hist_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
-                        uint32_t G, uint64_t *counts, uint32_t *blk, cudaStream_t st) {
+                        const BucketRange &R, uint32_t G, uint64_t *counts, uint32_t *blk,
+                        uint32_t *status, cudaStream_t st) {
     const uint64_t chunk = (n + G - 1) / G;
-    k_fp_hist_blk<<<G, 512, (uint32_t)nb * 4, st>>>(keys, n, key_bytes, (uint32_t)nb, chunk,
-                                                    (unsigned long long *)counts, blk);
+    k_fp_hist_blk<<<G, 512, (uint32_t)nb * 4, st>>>(keys, n, key_bytes, (uint32_t)nb, R, chunk,
+                                                    (unsigned long long *)counts, blk, status);
     note_launches(1);
 }
 
-void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint32_t G,
-                        const uint64_t *bucket_off, uint32_t *blk, uint64_t *lo, uint8_t *bb,
-                        cudaStream_t st) {
+void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                        const BucketRange &R, uint32_t G, const uint64_t *bucket_off, uint32_t *blk,
+                        uint64_t *lo, uint8_t *bb, uint32_t *status, cudaStream_t st) {
     const uint64_t chunk = (n + G - 1) / G;
     k_block_offsets<<<(uint32_t)((nb * 32 + 255) / 256), 256, 0, st>>>(blk, G, (uint32_t)nb, bucket_off);
     note_launches(1);
-    k_scatter_blk<<<G, 512, (uint32_t)nb * 4, st>>>(keys, n, key_bytes, (uint32_t)nb, chunk, blk, lo, bb);
+    k_scatter_blk<<<G, 512, (uint32_t)nb * 4, st>>>(keys, n, key_bytes, (uint32_t)nb, R, chunk, blk, lo,
+                                                    bb, status);
     note_launches(1);
 }
 
@@ -301,15 +319,15 @@ void launch_exclusive_scan(uint64_t *data, uint64_t len, uint64_t *tmp, cudaStre
 
 // ---------------------------------------------------------------------------
 // Scatter: lo word and rotation bit of every key to its bucket's range.
-__global__ void k_scatter(const void *keys, uint64_t n, uint32_t kb, uint64_t nb,
+__global__ void k_scatter(const void *keys, uint64_t n, uint32_t kb, uint64_t nb, BucketRange R,
                           const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo_out,
-                          uint8_t *bb_out) {
+                          uint8_t *bb_out, uint32_t *status) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t w0, w1, hi, lo;
+        uint64_t w0, w1, hi, lo, b;
         load_key(keys, i, kb, w0, w1);
         fingerprint(w0, w1, hi, lo);
-        uint64_t b = mulhi64(hi, nb);
+        if (!local_bucket(R, hi, nb, status, b)) continue;
         uint64_t p = bucket_off[b] + atomicAdd(&cursor[b], 1u);
         lo_out[p] = lo;
         bb_out[p] = (uint8_t)(hi & 1);
@@ -317,10 +335,11 @@ __global__ void k_scatter(const void *keys, uint64_t n, uint32_t kb, uint64_t nb
 }
 
 void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
-                    const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo, uint8_t *bb,
-                    cudaStream_t st) {
+                    const BucketRange &R, const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo,
+                    uint8_t *bb, uint32_t *status, cudaStream_t st) {
     if (n == 0) return;
-    k_scatter<<<grid_for(n, 256), 256, 0, st>>>(keys, n, key_bytes, nb, bucket_off, cursor, lo, bb);
+    k_scatter<<<grid_for(n, 256), 256, 0, st>>>(keys, n, key_bytes, nb, R, bucket_off, cursor, lo, bb,
+                                                status);
     note_launches(1);
 }
 
@@ -369,69 +388,13 @@ struct DivRT {
 };
 
 // ---------------------------------------------------------------------------
-// The node hash mix64(x + s) on 32-bit halves.  The search is bound by the
-// integer ALU pipe, so the 32-bit pieces of the 64-bit xor-shifts
-// z ^= z >> k (lo >> k, hi << (32 - k), hi >> k) are computed as products
-// with the runtime constant 2^(32 - k) on the multiply pipe, which would
-// otherwise idle; only the xors stay on the ALU pipe.  MPHF_EVAL selects
-// the instruction mix (0: plain 64-bit C; 1: wide multiply for the high
-// word; 2: three 32-bit multiplies; 3: like 2 for the last xor-shift too).
-#ifndef MPHF_EVAL
-#define MPHF_EVAL 0
-#endif
-#ifndef MPHF_RTC
-#define MPHF_RTC 1
-#endif
-#ifndef MPHF_RED_MODE
-#define MPHF_RED_MODE 1
-#endif
-
-__device__ __forceinline__ void xorshift_mul(uint32_t &zl, uint32_t &zh, uint32_t k) {
-    uint32_t a, b, c;
-#if MPHF_EVAL == 1
-    uint64_t w;
-    asm("mul.wide.u32 %0, %1, %2;" : "=l"(w) : "r"(zh), "r"(k));
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(a) : "r"(zl), "r"(k));
-    b = (uint32_t)w;
-    c = (uint32_t)(w >> 32);
-#else
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(a) : "r"(zl), "r"(k));  // lo >> s
-    asm("mul.lo.u32 %0, %1, %2;" : "=r"(b) : "r"(zh), "r"(k));  // hi << (32 - s)
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(c) : "r"(zh), "r"(k));  // hi >> s
-#endif
-    zl ^= a | b;
-    zh ^= c;
-}
-
-__device__ __forceinline__ void mul64_const(uint32_t &zl, uint32_t &zh, uint32_t cl, uint32_t ch) {
-    uint64_t w = (uint64_t)zl * cl;
-    uint32_t nh = (uint32_t)(w >> 32) + zl * ch + zh * cl;
-    zl = (uint32_t)w;
-    zh = nh;
-}
-
+// The node hash (Section 2.2, "a hash function modulo l"): h = mix64(x + s),
+// handed on as its two 32-bit halves for the reduction modulo the node size.
 struct Mixer {
-    uint32_t k30, k27, k31;  // 2^2, 2^5, 2^1, held in registers (kernel arguments)
     __device__ __forceinline__ void operator()(uint64_t z, uint32_t &hl, uint32_t &hh) const {
-#if MPHF_EVAL == 0
-        uint64_t h = mix64(z);
+        const uint64_t h = mix64(z);
         hl = (uint32_t)h;
         hh = (uint32_t)(h >> 32);
-#else
-        uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
-        xorshift_mul(zl, zh, k30);
-        mul64_const(zl, zh, 0x1CE4E5B9u, 0xBF58476Du);
-        xorshift_mul(zl, zh, k27);
-        mul64_const(zl, zh, 0x133111EBu, 0x94D049BBu);
-#if MPHF_EVAL == 3
-        xorshift_mul(zl, zh, k31);
-        hl = zl;
-        hh = zh;
-#else
-        hl = zl ^ ((zl >> 31) | (zh << 1));
-        hh = zh ^ (zh >> 31);
-#endif
-#endif
     }
 };
 
@@ -456,13 +419,8 @@ __device__ __forceinline__ uint32_t mod_halves(const ModCTR<MM> &r, uint32_t hl,
     if constexpr ((MM & (MM - 1)) == 0) {
         return hl & (MM - 1);
     } else {
-#if MPHF_RTC
         const uint32_t c = r.c;
-#else
-        constexpr uint32_t c = (uint32_t)((1ull << 32) % MM);
-#endif
         uint64_t t = (uint64_t)hh * c + hl;
-#if MPHF_RED_MODE == 1
         // c = 2^k for every full node size of the benchmarks (32 at 112, 256
         // at 560, 16 at 60 and 240, 64 at 96): fold t = th 2^32 + tl as
         // tl + th 2^k on the ALU, with the carry folded once more
@@ -475,7 +433,6 @@ __device__ __forceinline__ uint32_t mod_halves(const ModCTR<MM> &r, uint32_t hl,
             const uint32_t v = ul + (ul < add ? cc : 0u);  // carry out of 2^32 is worth c
             return v % MM;
         }
-#endif
         uint64_t u = (uint64_t)(uint32_t)(t >> 32) * c + (uint32_t)t;
         uint32_t v = (uint32_t)(u >> 32) * c + (uint32_t)u;
         return v % MM;
@@ -499,13 +456,7 @@ __device__ __forceinline__ ModCTR<MM> make_modct(uint32_t c_from_memory) {
 // (2^w - 1) < 0 keys (p_last <= unit <= 2^w - 2).
 // The whole chunk of seeds is decided before the next one starts, so the
 // smallest working seed wins.
-#ifndef MPHF_UNROLL
-#define MPHF_UNROLL 8
-#endif
-#ifndef MPHF_PAIRS
-#define MPHF_PAIRS 1
-#endif
-constexpr int kKeyUnroll = MPHF_UNROLL;  // key-loop unroll factor of the split search
+constexpr int kKeyUnroll = 8;  // key-loop unroll factor of the split search
 
 // SPT seeds per thread and round: two independent hash chains per key load
 // pay off where trials are many (the full nodes of l = 16); one keeps the
@@ -528,7 +479,6 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
                 cnt[j] += lut[div(mod_halves(mod, hl, hh))];
             }
         };
-#if MPHF_PAIRS
         // xs is 16-byte aligned: two keys per shared-memory load
         const ulonglong2 *xs2 = (const ulonglong2 *)xs;
 #pragma unroll kKeyUnroll
@@ -538,10 +488,6 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
             eval(q.y);
         }
         if (m & 1) eval(xs[m - 1]);
-#else
-#pragma unroll kKeyUnroll
-        for (uint32_t i = 0; i < m; i++) eval(xs[i]);
-#endif
         uint64_t best = ~0ull;
 #pragma unroll
         for (int j = SPT - 1; j >= 0; j--)
@@ -1066,7 +1012,7 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
     uint64_t x = 0;
     bool limit = false;
     const ModRT mrt{m, d.mod_c[m], d.mod_M[m]};  // from the table: no divisions per node
-    const Mixer mx{d.k30, d.k27, d.k31};
+    const Mixer mx{};
     if (kind == NODE_UPPER) {
         x = search_upper(xs, m, mrt, upper_left(sh, m), mx, d.max_value, limit, S);
     } else {
@@ -1168,7 +1114,7 @@ template <int LEAF>
 __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, const SmemArrays &A, BlockState &S) {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t salt = level_salt(0);
-    const Mixer mx{d.k30, d.k27, d.k31};
+    const Mixer mx{};
     for (;;) {
         uint32_t j = 0;
         if (lane == 0) j = atomicAdd(&S.leaf_next, 1u);

@@ -7,7 +7,13 @@ namespace rs {
 
 // Device status bits of one build (host maps them to error codes with the
 // precedence bucket size > duplicate > search cap > wait timeout).
-enum : uint32_t { ST_BUCKET = 1u, ST_DUPLICATE = 2u, ST_LIMIT = 4u, ST_TIMEOUT = 8u };
+enum : uint32_t { ST_BUCKET = 1u, ST_DUPLICATE = 2u, ST_LIMIT = 4u, ST_TIMEOUT = 8u, ST_RANGE = 16u };
+
+// Buckets a build covers: the consecutive range [b_lo, b_lo + nb) of a function
+// whose keys hash to nb_hash buckets (b_lo = 0, nb_hash = nb for a whole function).
+struct BucketRange {
+    uint64_t nb_hash, b_lo;
+};
 
 // Per-build descriptor read by the search kernel (one per instance of a batch).
 struct InstDesc {
@@ -23,7 +29,6 @@ struct InstDesc {
     uint32_t leaf, bij;          // bij: MPHF_BIJECTION_* leaf method
     uint32_t tree;               // MPHF_TREE_*: lower aggregation levels or fanout 2 everywhere
     uint32_t nb;
-    uint32_t k30, k27, k31;      // 4, 32, 2: multipliers of the hash's xor-shifts
     uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
     uint32_t leaf_method;        // 0 lock-step, 1 early rejection, 2 early rejection + table
     const uint8_t *rot_canon;    // per m <= 16 at offset 2^m - 4: canonical rotation of x
@@ -49,17 +54,18 @@ void note_launches(uint64_t k);
 uint64_t launches_total();
 
 // Stage launchers (all asynchronous on `st`).
-void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint64_t *counts,
-                    cudaStream_t st);
+void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                    const BucketRange &R, uint64_t *counts, uint32_t *status, cudaStream_t st);
 // Two-level counting sort (nb <= 8192): number of blocks for n keys, 0 when
 // the build must use launch_fp_hist / launch_scatter instead.  blk holds
 // G * nb counters.
 uint32_t sort_blocks(uint64_t n, uint64_t nb);
-void launch_fp_hist_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint32_t G,
-                        uint64_t *counts, uint32_t *blk, cudaStream_t st);
-void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb, uint32_t G,
-                        const uint64_t *bucket_off, uint32_t *blk, uint64_t *lo, uint8_t *bb,
-                        cudaStream_t st);
+void launch_fp_hist_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                        const BucketRange &R, uint32_t G, uint64_t *counts, uint32_t *blk,
+                        uint32_t *status, cudaStream_t st);
+void launch_scatter_blk(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
+                        const BucketRange &R, uint32_t G, const uint64_t *bucket_off, uint32_t *blk,
+                        uint64_t *lo, uint8_t *bb, uint32_t *status, cudaStream_t st);
 void launch_plan(const uint64_t *counts, uint64_t nb, const uint32_t *nodes_tab, uint64_t *node_cnt,
                  uint32_t *status, uint32_t *max_m, uint64_t *size_hist, cudaStream_t st);
 // Work items of one instance ordered by decreasing bucket size; size_off is
@@ -72,8 +78,8 @@ void launch_items_by_size(const uint64_t *bucket_off, uint64_t nb, const uint64_
 uint64_t scan_tmp_words(uint64_t len);
 void launch_exclusive_scan(uint64_t *data, uint64_t len, uint64_t *tmp, cudaStream_t st);
 void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t nb,
-                    const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo, uint8_t *bb,
-                    cudaStream_t st);
+                    const BucketRange &R, const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo,
+                    uint8_t *bb, uint32_t *status, cudaStream_t st);
 SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads, uint32_t blocks_per_sm);
 void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
                    const SearchLaunch &L, cudaStream_t st);
@@ -95,6 +101,17 @@ void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint
 void launch_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel, cudaStream_t st);
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
                   uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st);
+
+// Building one function on several GPUs (bucket ranges, Section 5.2).
+// Keys grouped by the rank owning their bucket (nb buckets, `world` ranges):
+// counts[r] += keys of rank r; then each key to cursor[r]++ in `out`.
+void launch_route_count(const uint64_t *keys, uint64_t n, uint32_t kb, uint64_t nb, uint32_t world,
+                        uint64_t *counts, cudaStream_t st);
+void launch_route_scatter(const uint64_t *keys, uint64_t n, uint32_t kb, uint64_t nb, uint32_t world,
+                          uint64_t *cursor, uint64_t *out, cudaStream_t st);
+void launch_shard_offsets(const uint64_t *in, uint64_t count, uint64_t base, uint64_t *out,
+                          cudaStream_t st);
+void launch_shard_bits(const uint64_t *in, uint64_t bits, uint64_t at, uint64_t *out, cudaStream_t st);
 
 // Query side.
 struct QueryView {

@@ -159,6 +159,10 @@ SIGNATURES = {
     "mphf_server_submit": (_I, [_P, _P, _P]),
     "mphf_server_poll": (_I, [_P, _U64, _U32, _P, _P, _P]),
     "mphf_server_destroy": (_I, [_P]),
+    "mphf_shard_route": (_I, [_P, _U64, _U32, _U64, _U32, _U32, _P, _P, _P]),
+    "mphf_build_shard": (_I, [_P, _U64, _U64, _P, _U32, _U32, _P, _P]),
+    "mphf_shard_pack": (_I, [_P, _P, _P, _P]),
+    "mphf_shard_concat": (_I, [_P, _P, _U32, _P, _P, _P]),
 }
 
 
