@@ -6,8 +6,10 @@
 One step = one complete build (fingerprint, bucket sort, split and leaf
 searches with rotation fitting, Golomb-Rice / Elias-Fano packing) of the
 10,000,000-key workload with leaf size 16 and bucket size 2000, keys already
-resident in device memory.  Prints one JSON line (rank 0).  N > 1 runs one
-independent build per GPU (weak scaling, no collective on the data path).
+resident in device memory.  Prints one JSON line (rank 0).  N > 1 builds one
+function over N x 10,000,000 keys (each rank holds its own 10^7), sharded by
+bucket ranges across the GPUs (Section 5.2): one all-to-all of keys, one
+all-gather of the packed shards (weak scaling: keys per GPU fixed).
 
 --impl reference times the CPU oracle on the host cores on a bounded bucket
 sample of the same workload.
@@ -109,6 +111,8 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the key count (profiling runs)")
     ap.add_argument("--mode", choices=["build", "serve", "batch", "peaks"], default="build")
     ap.add_argument("--requests", type=int, default=24, help="serve mode: requests per run")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests of the serve leg in the default run (0 = skip)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: Poisson arrivals per second")
     ap.add_argument("--batch-builds", type=int, default=128,
                     help="builds in the batched-vs-plain comparison (0 = skip); batch mode: 4096")
@@ -237,8 +241,11 @@ def batch_vs_plain(M, torch, count: int, hi_exp: float = 5.0) -> dict:
             "batched_over_plain": t_plain / t_batch, "identical": identical}
 
 
-def serve_run(M, torch, keys, leaf, arrivals) -> dict:
-    srv = M.Server(executors=2, max_batch=64)
+def serve_run(M, torch, keys, leaf, arrivals, plain=None) -> dict:
+    """Requests submitted at their arrival times to one server; with `plain`
+    (a list of functions built one by one from the same keys), every served
+    function is compared with its plain build word for word."""
+    srv = M.Server()
     tickets = []
     start = time.perf_counter()
     for dk, at in zip(keys, arrivals):
@@ -259,6 +266,10 @@ def serve_run(M, torch, keys, leaf, arrivals) -> dict:
     ok = all(r[0] == M.OK for r in res.values())
     bad = sum(r[1].verify(dk) if r[1] is not None else 1
               for r, dk in zip((res[t] for t in tickets), keys))
+    identical = None
+    if plain is not None:
+        identical = all(res[t][1] is not None and same_function(res[t][1], g)
+                        for t, g in zip(tickets, plain))
     for r in res.values():
         if r[1] is not None:
             r[1].close()
@@ -266,37 +277,60 @@ def serve_run(M, torch, keys, leaf, arrivals) -> dict:
     n = sum(int(k.shape[0]) for k in keys)
     return {"requests": len(keys), "keys": n, "keys_per_s": n / (last - first),
             "requests_per_s": len(keys) / (last - first), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "all_ok": ok and bad == 0}
+            "p99_s": float(np.percentile(lat, 99)), "all_ok": ok and bad == 0,
+            "identical_to_plain": identical}
 
 
-def run_serve(args):
-    """Serve workload: Poisson arrivals of 16-byte-key builds, n = floor(10^U(4,7)),
-    l = 16, b = 2000; keys resident on the device before the clock starts."""
-    import torch
-    from paper_2212_09562_b300 import mphf as M
-    M.lib()
+def serve_leg(M, torch, requests: int, rate: float) -> dict:
+    """The serve workload (Poisson arrivals at `rate`, 16-byte keys, n =
+    floor(10^U(4,7)), l = 16, b = 2000), keys resident on the device: the
+    same requests built one by one with plain builds, then served at the
+    offered rate and again paced at 0.8x the served capacity; every served
+    function equals its plain build."""
     seed = W.SEED_BASE + 5
-    sizes = W.serve_sizes(args.requests, seed)
+    sizes = W.serve_sizes(requests, seed)
     keys = [torch.from_numpy(W.distinct_bytes16(int(n), seed * 1000 + i)).cuda()
             for i, n in enumerate(sizes)]
-    warm = M.Server(executors=1)
+    warm = M.Server()
     t = warm.submit(keys[0][:5000], 16, 2000)
     while warm.poll(t, 100) is None:
         pass
     warm.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [M.MPHF.build(k, 16, 2000, True) for k in keys]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    n = sum(int(k.shape[0]) for k in keys)
+    offered = serve_run(M, torch, keys, 16, W.poisson_arrivals(requests, rate, seed), plain)
+    rate2 = 0.8 * offered["requests_per_s"]
+    paced = serve_run(M, torch, keys, 16, W.poisson_arrivals(requests, rate2, seed + 1), plain)
+    for g in plain:
+        g.close()
+    return {"requests": requests, "keys": n, "rate_per_s": rate,
+            "sizes": "floor(10^U(4,7)) 16-byte keys, l=16, b=2000",
+            "served_keys_per_s": offered["keys_per_s"], "plain_keys_per_s": n / t_plain,
+            "served_over_plain": offered["keys_per_s"] / (n / t_plain),
+            "p50_s": offered["p50_s"], "p99_s": offered["p99_s"],
+            "identical": bool(offered["identical_to_plain"] and paced["identical_to_plain"]),
+            "offered_rate": offered, "paced_at_0.8x_capacity": dict(paced, rate_per_s=rate2)}
+
+
+def run_serve(args):
+    """Serve workload alone (bench.py --mode serve)."""
+    import torch
+    from paper_2212_09562_b300 import mphf as M
+    M.lib()
     sampler = ClockSampler(0)
     sampler.start()
-    offered = serve_run(M, torch, keys, 16, W.poisson_arrivals(args.requests, args.rate, seed))
-    rate2 = 0.8 * offered["requests_per_s"]
-    paced = serve_run(M, torch, keys, 16, W.poisson_arrivals(args.requests, rate2, seed + 1))
+    r = serve_leg(M, torch, args.requests, args.rate)
     clocks = sampler.stop()
     out = {"metric": "served MPHF build keys/s (l=16, b=2000, 16-byte keys, Poisson arrivals)",
-           "value": offered["keys_per_s"], "unit": "keys/s", "n_gpus": 1, "higher_is_better": True,
+           "value": r["served_keys_per_s"], "unit": "keys/s", "n_gpus": 1, "higher_is_better": True,
            "dtype": "u64", "data": "synthetic",
            "config": {"workload": "serve", "requests": args.requests, "rate_per_s": args.rate,
-                      "sizes": "floor(10^U(4,7)) 16-byte keys", "executors": 2},
-           "offered_rate": offered, "paced_at_0.8x_capacity": dict(paced, rate_per_s=rate2),
-           "clocks": clocks}
+                      "sizes": r["sizes"]},
+           "serve": r, "clocks": clocks}
     print(json.dumps(out), flush=True)
 
 
@@ -386,7 +420,7 @@ def query_throughput(torch, g, dkeys, stream, reps: int = 5) -> dict:
 
 
 def rank_keys(w, rank: int) -> np.ndarray:
-    """Each rank builds its own key set (weak scaling: independent builds)."""
+    """Each rank's own slice of the key set (weak scaling: w.n keys per rank)."""
     return W.keys_for(w) if rank == 0 else W.random_keys(w.n, w.key_bytes, w.seed + rank)
 
 
@@ -436,61 +470,83 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    from paper_2212_09562_b300 import shard as S
+
+    def one_build(k):
+        """(function, the part this rank searched): the whole build on one GPU,
+        else one function over all ranks' keys in bucket-range shards."""
+        if world == 1:
+            g = M.MPHF.build(k, w.leaf, w.bucket, w.rotation, tree=w.tree)
+            return g, g
+        return S.build_sharded(k, w.leaf, w.bucket, w.rotation, tree=w.tree)
+
+    def close(g, sh):
+        if sh is not g:
+            sh.close()
+        g.close()
+
     for i in range(args.warmup):
-        M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation, tree=w.tree).close()
+        close(*one_build(dkeys))
     peaks = measured_int_peaks()  # before the timed region, on this GPU
     sampler = ClockSampler(local)
     sampler.start()
-    step_ms, search_ms, evals, trials = [], [], 0, 0
-    launches0 = M.kernel_launches()
+    step_ms, search_ms, evals, trials, my_evals, launches = [], [], 0, 0, 0, 0
     barrier()
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (outside the step's events)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = M.kernel_launches()
         ev0.record(stream)
-        g = M.MPHF.build(dkeys, w.leaf, w.bucket, w.rotation, tree=w.tree)
+        g, sh = one_build(dkeys)
         ev1.record(stream)
         ev1.synchronize()
+        launches += M.kernel_launches() - l0
         step_ms.append(ev0.elapsed_time(ev1))
-        st = g.stats()
-        search_ms.append(st["ms"]["search"])
-        evals += sum(st[k][1] for k in ("leaf", "lower1", "lower2", "upper"))
+        st, mine = g.stats(), sh.stats()
+        search_ms.append(mine["ms"]["search"])
+        evals += sum(st[k][1] for k in ("leaf", "lower1", "lower2", "upper"))  # all ranks'
         trials += sum(st[k][0] for k in ("leaf", "lower1", "lower2", "upper"))
+        my_evals += sum(mine[k][1] for k in ("leaf", "lower1", "lower2", "upper"))
         if i == args.steps - 1:
             bad = g.verify(dkeys)
-            assert bad == 0, f"built function is not a bijection ({bad} bad keys)"
-            stages = st["ms"]
+            assert bad == 0, f"built function is not injective on this rank's keys ({bad} bad keys)"
+            stages = mine["ms"]
             query = query_throughput(torch, g, dkeys, stream)
-        g.close()
+        close(g, sh)
     barrier()
     wall = time.perf_counter() - t_wall
-    launches = M.kernel_launches() - launches0 - 3  # minus the final verify's query/mark/memset-free
     clocks = sampler.stop()
     total_ms = max_over_ranks(sum(step_ms), world)
     keys_per_s = weak_scaling_value(world, args.steps, w.n, total_ms)
 
-    # end to end through the public host-buffer call: pinned keys in, packed function out
+    # end to end through the public API from pinned host keys: one GPU calls
+    # mphf_build_host; N GPUs copy their keys in and build the sharded function;
+    # the packed function comes back to the host
     e2e = None
     if args.e2e_steps > 0:
         pinned = torch.from_numpy(keys.view(np.int64) if keys.ndim == 1 else keys).pin_memory()
         host_view = pinned.numpy().view(np.uint64) if keys.ndim == 1 else pinned.numpy()
         times, d2h = [], 0
         for _ in range(args.e2e_steps):
-            torch.cuda.synchronize()
+            barrier()
             t0 = time.perf_counter()
-            g = M.MPHF.build_host(host_view, w.leaf, w.bucket, w.rotation, tree=w.tree)
+            if world == 1:
+                g = M.MPHF.build_host(host_view, w.leaf, w.bucket, w.rotation, tree=w.tree)
+                sh = g
+            else:
+                g, sh = one_build(pinned.cuda(non_blocking=True))
             blob = g.serialize()
-            times.append(time.perf_counter() - t0)
+            times.append(max_over_ranks(time.perf_counter() - t0, world))
             d2h = len(blob)
-            g.close()
+            close(g, sh)
         e2e = {"value": world * w.n / statistics.mean(times), "unit": "keys/s",
-               "h2d_bytes_per_step": int(keys.nbytes), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(keys.nbytes) * world, "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
         return
     mean_search = statistics.mean(search_ms)
-    evals_per_build = evals / args.steps
+    evals_per_build = my_evals / args.steps  # this rank's search launch
     roof = search_roofline(peaks, evals_per_build, mean_search, clocks.get("sm_mhz"),
                            SEARCH_DRAM_BYTES_PER_KEY * w.n if w.name.startswith("rot_l16") else None)
     out = {"metric": METRIC, "value": keys_per_s, "unit": "keys/s", "n_gpus": world,
@@ -502,13 +558,17 @@ def run_ours(args):
                       "tree": "fanout 2" if w.tree else "lower aggregation levels",
                       "key_bytes": w.key_bytes,
                       "l2": "flushed between steps (256 MB write)",
-                      "parallelism": f"{world} independent builds (one per GPU)"},
-           "trials_per_s": world * trials / (total_ms / 1000.0),
-           "evals_per_s": world * evals / (total_ms / 1000.0),
+                      "parallelism": ("1 GPU" if world == 1 else
+                                      f"{world} GPUs: one function of {world} x {w.n} keys in "
+                                      "bucket-range shards (all-to-all of keys, all-gather of shards)")},
+           "trials_per_s": trials / (total_ms / 1000.0),
+           "evals_per_s": evals / (total_ms / 1000.0),
            "search_ms": mean_search, "wall_s": wall, "stage_ms": stages, "query": query,
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if world == 1 and args.batch_builds > 0:
         out["batch"] = batch_vs_plain(M, torch, args.batch_builds)
+    if world == 1 and args.serve_requests > 0:
+        out["serve"] = serve_leg(M, torch, args.serve_requests, args.rate)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, keys, args.cpu_seconds)
         out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -363,19 +363,36 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
                      int *statuses);
 
 /* ---------------------------------------------------------------------------
- * Serving: a build server with continuous batching.  Requests are queued;
- * executor threads (one CUDA stream each) take every pending request that
- * fits into free device memory and build them together as one batch (one
- * persistent search over all their buckets).  A batch is admitted while
- * another is still on the device, so their work overlaps.  Results are
- * identical to building each request alone.  No device-side waiting is
- * involved; every host wait is bounded by the caller's timeout. */
+ * Serving: a build server with continuous batching (the paper has no
+ * counterpart; its builds are one at a time).  One serving search kernel
+ * stays on the device while there is work and takes buckets from a queue in
+ * device memory.  A control thread admits queued requests in arrival order
+ * while a request slot and device memory are free, prepares them (the
+ * fingerprint, bucket sort and plan kernels run beside the search on the SM
+ * room it leaves), feeds their buckets into the queue a few at a time from
+ * each running request in turn, and packs each request as soon as its own
+ * last bucket is done.  So requests that arrive while others are on the
+ * device join the running search, and each completes on its own.  Results
+ * are identical to building each request alone.  The search leaves the
+ * device when no request is left.  Every device wait is bounded (a search
+ * block waits at most idle_ms for work); every host wait is bounded by the
+ * caller's timeout. */
 typedef struct mphf_server mphf_server_t;
 
+#define MPHF_SERVER_MAX_REQUESTS 1024u
+
 typedef struct {
-    uint32_t executors;          /* batches on the device at once (default 2)          */
-    uint32_t max_batch;          /* requests per batch (default 64)                    */
-    uint64_t hbm_reserve_bytes;  /* device memory kept free (default 1 GiB)            */
+    uint32_t max_requests;       /* requests on the device at once (default 64, at most
+                                    MPHF_SERVER_MAX_REQUESTS)                           */
+    uint32_t reserved_sms;       /* SMs on which the search keeps one block slot free for
+                                    the other requests' preparation and packing (default 4
+                                    when the whole cfg is NULL; 0 allowed)              */
+    uint64_t hbm_reserve_bytes;  /* device memory kept free (default 1 GiB)             */
+    uint32_t idle_ms;            /* bound on a search block's wait for work while the server
+                                    is silent (default 10000, at most 600000); the server
+                                    stops the search itself whenever no request is left */
+    uint32_t threads;            /* search block size, a multiple of 32 in 64..512
+                                    (default 512)                                       */
 } mphf_server_cfg;
 
 /* Submit/admit/finish times of a request, seconds since the server started. */

@@ -342,6 +342,9 @@ struct Job {
     uint32_t sort_g = 0;
     uint16_t *node_m = nullptr;
     uint64_t n_nodes = 0;
+    uint32_t max_m = 0;    // largest bucket
+    bool planned = false;  // its buckets are counted in the pass's work-order histogram
+    InstDesc desc{};       // what the search kernel reads about this job
 };
 
 // Parameters of a build apart from where its keys are.
@@ -389,50 +392,76 @@ void fail_job(Job &j, int rc, Mem &mem) {
     }
 }
 
-// Runs every job; afterwards each job has rc set and, if rc is OK, h built.
-// Returns a code for failures that affect all jobs (CUDA errors), else OK.
-int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shared_alloc,
-             uint32_t threads, uint32_t blocks_per_sm) {
-    Mem mem{shared_alloc, st};
-    int grc = MPHF_OK;
-    const size_t J = jobs.size();
+// Scratch shared by the jobs of one engine pass: the prefix-sum scratch, the
+// bucket-size histogram of the work order, and a pinned host buffer for the
+// totals read between phases (four words per job).
+struct EngineCtx {
+    Mem mem;
     uint64_t *host = nullptr, *scan_tmp = nullptr, *size_hist = nullptr;
-    uint32_t *size_cursor = nullptr, *head = nullptr;
-    InstDesc *d_inst = nullptr;
-    WorkItem *items = nullptr;
-    std::vector<InstDesc> hinst;
-    std::vector<uint32_t> inst_job;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    uint64_t max_nb = 0, total_items = 0, total_slots = 0;
-    uint32_t max_m = 0;
-    bool wide_lower = false;  // some build has lower-level nodes of l >= 14
-    float ms[4] = {0, 0, 0, 0};
-#define CU(x)                    \
-    do {                         \
-        if ((x) != cudaSuccess) { \
-            cudaGetLastError();  \
-            grc = MPHF_ECUDA;    \
-            goto done;           \
-        }                        \
-    } while (0)
-    for (auto &e : ev) cudaEventCreate(&e);
-    cudaEventRecord(ev[0], st);
-    for (auto &j : jobs) max_nb = j.nb > max_nb ? j.nb : max_nb;
-    CU(cudaMallocHost(&host, 8 * 4 * (J ? J : 1)));
-    scan_tmp = (uint64_t *)mem.get((scan_tmp_words((max_nb + 2 > 4098 ? max_nb + 2 : 4098)) + 64) * 8);
-    size_hist = (uint64_t *)mem.get(4098 * 8);
-    size_cursor = (uint32_t *)mem.get(4097 * 4);
-    head = (uint32_t *)mem.get(64);
-    if (!scan_tmp || !size_hist || !size_cursor || !head) {
-        grc = MPHF_ENOMEM;
-        goto done;
-    }
-    CU(cudaMemsetAsync(size_hist, 0, 4098 * 8, st));
-    CU(cudaMemsetAsync(size_cursor, 0, 4097 * 4, st));
-    CU(cudaMemsetAsync(head, 0, 64, st));
+    uint32_t *size_cursor = nullptr;
+    size_t cap_jobs = 0;
+    uint64_t cap_nb = 0;
 
-    // phase 1: fingerprints, bucket sizes, plan, offsets (per job, no host reads)
-    for (auto &j : jobs) {
+    // Room for `jobs` jobs of at most max_nb buckets each.
+    int reserve(size_t jobs, uint64_t max_nb) {
+        if (jobs > cap_jobs) {
+            if (host) cudaFreeHost(host);
+            host = nullptr;
+            cap_jobs = 0;
+            if (cudaMallocHost(&host, 8 * 4 * (jobs ? jobs : 1)) != cudaSuccess) {
+                cudaGetLastError();
+                return MPHF_ECUDA;
+            }
+            cap_jobs = jobs;
+        }
+        if (!scan_tmp || max_nb > cap_nb) {
+            mem.put(scan_tmp);
+            const uint64_t len = max_nb + 2 > 4098 ? max_nb + 2 : 4098;
+            scan_tmp = (uint64_t *)mem.get((scan_tmp_words(len) + 64) * 8);
+            cap_nb = max_nb;
+        }
+        if (!size_hist) size_hist = (uint64_t *)mem.get(4098 * 8);
+        if (!size_cursor) size_cursor = (uint32_t *)mem.get(4097 * 4);
+        return scan_tmp && size_hist && size_cursor ? MPHF_OK : MPHF_ENOMEM;
+    }
+    // The work-order histogram starts empty for every pass.
+    int clear_order() {
+        if (cudaMemsetAsync(size_hist, 0, 4098 * 8, mem.st) != cudaSuccess ||
+            cudaMemsetAsync(size_cursor, 0, 4097 * 4, mem.st) != cudaSuccess) {
+            cudaGetLastError();
+            return MPHF_ECUDA;
+        }
+        return MPHF_OK;
+    }
+    void release() {
+        mem.put(scan_tmp);
+        mem.put(size_hist);
+        mem.put(size_cursor);
+        scan_tmp = size_hist = nullptr;
+        size_cursor = nullptr;
+        cudaStreamSynchronize(mem.st);
+        if (host) cudaFreeHost(host);
+        host = nullptr;
+        cap_jobs = 0;
+        cap_nb = 0;
+    }
+};
+
+#define CU(x)                     \
+    do {                          \
+        if ((x) != cudaSuccess) { \
+            cudaGetLastError();   \
+            return MPHF_ECUDA;    \
+        }                         \
+    } while (0)
+
+// Phase 1 (fingerprints, bucket sizes, plan, offsets) of every live job, then
+// one host read of each job's node total, largest bucket and status.
+// Jobs that fail get rc set; the return value is a failure of all of them.
+int phase_plan(std::vector<Job *> &jobs, EngineCtx &c) {
+    const cudaStream_t st = c.mem.st;
+    for (Job *jp : jobs) {
+        Job &j = *jp;
         if (j.rc) continue;
         mphf_t *h = j.h;
         Mem jm{h->has_alloc ? &h->alloc : nullptr, st};
@@ -440,16 +469,16 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         h->cum_keys = (uint64_t *)jm.get((nb + 1) * 8);
         h->node_off = (uint64_t *)jm.get((nb + 1) * 8);
         h->bit_pos = (uint64_t *)jm.get((nb + 1) * 8);
-        j.cursor = (uint32_t *)mem.get((nb + 1) * 4);
-        j.small = (uint32_t *)mem.get(64);
-        j.lo_s = (uint64_t *)mem.get(j.n * 8);
-        j.bb_s = (uint8_t *)mem.get(j.n);
-        j.counters = (uint64_t *)mem.get(64);
+        j.cursor = (uint32_t *)c.mem.get((nb + 1) * 4);
+        j.small = (uint32_t *)c.mem.get(64);
+        j.lo_s = (uint64_t *)c.mem.get(j.n * 8);
+        j.bb_s = (uint8_t *)c.mem.get(j.n);
+        j.counters = (uint64_t *)c.mem.get(64);
         j.sort_g = sort_blocks(j.n, nb);
-        if (j.sort_g) j.blk = (uint32_t *)mem.get((uint64_t)j.sort_g * nb * 4);
+        if (j.sort_g) j.blk = (uint32_t *)c.mem.get((uint64_t)j.sort_g * nb * 4);
         if (!h->cum_keys || !h->node_off || !h->bit_pos || !j.cursor || !j.small || !j.lo_s ||
             !j.bb_s || !j.counters || (j.sort_g && !j.blk)) {
-            fail_job(j, MPHF_ENOMEM, mem);
+            fail_job(j, MPHF_ENOMEM, c.mem);
             continue;
         }
         CU(cudaMemsetAsync(h->cum_keys, 0, (nb + 1) * 8, st));
@@ -462,41 +491,44 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
                                j.small, st);
         else
             launch_fp_hist(j.d_keys, j.n, j.p.key_bytes, nb, j.range, h->cum_keys, j.small, st);
-        launch_plan(h->cum_keys, nb, h->tabs.nodes, h->node_off, j.small, j.small + 1, size_hist, st);
-        launch_exclusive_scan(h->cum_keys, nb + 1, scan_tmp, st);
-        launch_exclusive_scan(h->node_off, nb + 1, scan_tmp, st);
+        launch_plan(h->cum_keys, nb, h->tabs.nodes, h->node_off, j.small, j.small + 1, c.size_hist, st);
+        j.planned = true;
+        launch_exclusive_scan(h->cum_keys, nb + 1, c.scan_tmp, st);
+        launch_exclusive_scan(h->node_off, nb + 1, c.scan_tmp, st);
         CU(cudaGetLastError());
     }
-    for (size_t i = 0; i < J; i++) {
-        Job &j = jobs[i];
+    for (size_t i = 0; i < jobs.size(); i++) {
+        Job &j = *jobs[i];
         if (j.rc) continue;
-        total_slots += j.nb;  // every bucket of these jobs is counted in size_hist
-        CU(cudaMemcpyAsync(host + 4 * i, j.h->node_off + j.nb, 8, cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(host + 4 * i + 1, j.small, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(c.host + 4 * i, j.h->node_off + j.nb, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(c.host + 4 * i + 1, j.small, 8, cudaMemcpyDeviceToHost, st));
     }
     CU(cudaStreamSynchronize(st));
-    cudaEventRecord(ev[1], st);
+    for (size_t i = 0; i < jobs.size(); i++) {
+        Job &j = *jobs[i];
+        if (j.rc) continue;
+        j.n_nodes = c.host[4 * i];
+        const uint32_t status = (uint32_t)c.host[4 * i + 1];
+        j.max_m = (uint32_t)(c.host[4 * i + 1] >> 32);
+        j.h->info.n_nodes = j.n_nodes;
+        j.h->info.max_bucket = j.max_m;
+        if (status) fail_job(j, status_code(status), c.mem);
+    }
+    return MPHF_OK;
+}
 
-    // phase 2: group keys by bucket; one persistent search over every job's buckets
-    launch_exclusive_scan(size_hist, 4098, scan_tmp, st);
-    for (size_t i = 0; i < J; i++) {
-        Job &j = jobs[i];
+// Phase 2: keys grouped by bucket and the search descriptor of every live job.
+int phase_scatter(std::vector<Job *> &jobs, EngineCtx &c) {
+    const cudaStream_t st = c.mem.st;
+    for (Job *jp : jobs) {
+        Job &j = *jp;
         if (j.rc) continue;
         mphf_t *h = j.h;
-        j.n_nodes = host[4 * i];
-        const uint32_t status = (uint32_t)host[4 * i + 1];
-        const uint32_t mm = (uint32_t)(host[4 * i + 1] >> 32);
-        h->info.n_nodes = j.n_nodes;
-        h->info.max_bucket = mm;
-        if (status) {
-            fail_job(j, status_code(status), mem);
-            continue;
-        }
         Mem jm{h->has_alloc ? &h->alloc : nullptr, st};
         h->values = (uint64_t *)jm.get(j.n_nodes * 8);
-        j.node_m = (uint16_t *)mem.get(j.n_nodes * 2);
+        j.node_m = (uint16_t *)c.mem.get(j.n_nodes * 2);
         if (!h->values || !j.node_m) {
-            fail_job(j, MPHF_ENOMEM, mem);
+            fail_job(j, MPHF_ENOMEM, c.mem);
             continue;
         }
         if (j.sort_g)
@@ -505,7 +537,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         else
             launch_scatter(j.d_keys, j.n, j.p.key_bytes, j.nb, j.range, h->cum_keys, j.cursor, j.lo_s,
                            j.bb_s, j.small, st);
-        InstDesc d;
+        InstDesc &d = j.desc;
         memset(&d, 0, sizeof(d));
         d.lo = j.lo_s;
         d.bb = j.bb_s;
@@ -530,127 +562,179 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         d.rot_canon = d.rot_period = nullptr;
         if (j.p.leaf_method == MPHF_LEAF_TABLE &&
             device_rot_tables(h->device, &d.rot_canon, &d.rot_period) != MPHF_OK) {
-            fail_job(j, MPHF_ENOMEM, mem);
+            fail_job(j, MPHF_ENOMEM, c.mem);
             continue;
         }
-        inst_job.push_back((uint32_t)i);
-        hinst.push_back(d);
-        total_items += j.nb;
-        max_m = mm > max_m ? mm : max_m;
-        if (j.p.tree_shape == MPHF_TREE_RECSPLIT && j.p.leaf_size >= 14) wide_lower = true;
-    }
-    if (total_slots > 0xFFFFFFFFull) {
-        grc = MPHF_EINVAL;
-        goto done;
-    }
-    if (total_items > 0) {
-        // slots of jobs that failed their plan stay empty (all-ones: skipped)
-        d_inst = (InstDesc *)mem.get(hinst.size() * sizeof(InstDesc));
-        items = (WorkItem *)mem.get(total_slots * sizeof(WorkItem));
-        if (!d_inst || !items) {
-            grc = MPHF_ENOMEM;
-            goto done;
-        }
-        CU(cudaMemsetAsync(items, 0xFF, total_slots * sizeof(WorkItem), st));
-        CU(cudaMemcpyAsync(d_inst, hinst.data(), hinst.size() * sizeof(InstDesc),
-                           cudaMemcpyHostToDevice, st));
-        for (size_t k = 0; k < inst_job.size(); k++) {
-            Job &j = jobs[inst_job[k]];
-            launch_items_by_size(j.h->cum_keys, j.nb, size_hist, size_cursor, items, (uint32_t)k, st);
-        }
-        // Default block size: the lower-level nodes of l >= 14 need hundreds of
-        // thousands of trials and fill 512 threads; smaller leaves and the
-        // fanout-2 tree do better with 256 (B300: l = 8 0.19 vs 0.30 ms,
-        // l = 12 15.6 both, fanout-2 l = 24 24.8 vs 28.3 ms; l = 16 8.85 s at
-        // 512 threads, two blocks per SM, against 9.22 s with one).
-        if (!threads) threads = wide_lower ? 512u : 256u;
-        SearchLaunch L = plan_search_launch(max_m, (uint32_t)total_slots, threads, blocks_per_sm);
-        cudaEventRecord(ev[2], st);
-        launch_search(d_inst, items, (uint32_t)total_slots, head, L, st);
         CU(cudaGetLastError());
-    } else {
-        cudaEventRecord(ev[2], st);
     }
-    cudaEventRecord(ev[3], st);
+    return MPHF_OK;
+}
 
-    // phase 3: Golomb-Rice lengths and offsets
-    for (size_t i = 0; i < J; i++) {
-        Job &j = jobs[i];
+// Phases 3 and 4 of every live job whose search has finished: Golomb-Rice
+// lengths and offsets, one host read of the bit totals and statuses, then
+// the Golomb-Rice bits, Elias-Fano sequences, directories and statistics.
+int phase_pack(std::vector<Job *> &jobs, EngineCtx &c) {
+    const cudaStream_t st = c.mem.st;
+    for (size_t i = 0; i < jobs.size(); i++) {
+        Job &j = *jobs[i];
         if (j.rc) continue;
         mphf_t *h = j.h;
         CU(cudaMemsetAsync(h->bit_pos, 0, (j.nb + 1) * 8, st));
         launch_gr_lengths(h->values, j.node_m, h->node_off, j.nb, h->tabs.tau, j.p.leaf_size,
                           j.p.leaf_bijection, h->bit_pos, st);
-        launch_exclusive_scan(h->bit_pos, j.nb + 1, scan_tmp, st);
+        launch_exclusive_scan(h->bit_pos, j.nb + 1, c.scan_tmp, st);
         CU(cudaGetLastError());
-        CU(cudaMemcpyAsync(host + 4 * i, h->bit_pos + j.nb, 8, cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(host + 4 * i + 1, j.small, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(c.host + 4 * i, h->bit_pos + j.nb, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(c.host + 4 * i + 1, j.small, 8, cudaMemcpyDeviceToHost, st));
     }
     CU(cudaStreamSynchronize(st));
-
-    // phase 4: Golomb-Rice bits, Elias-Fano, rank directories, statistics
-    for (size_t i = 0; i < J; i++) {
-        Job &j = jobs[i];
+    for (size_t i = 0; i < jobs.size(); i++) {
+        Job &j = *jobs[i];
         if (j.rc) continue;
         mphf_t *h = j.h;
-        const uint32_t status = (uint32_t)host[4 * i + 1];
+        const uint32_t status = (uint32_t)c.host[4 * i + 1];
         if (status) {
-            fail_job(j, status_code(status), mem);
+            fail_job(j, status_code(status), c.mem);
             continue;
         }
-        const uint64_t gr_bits = host[4 * i];
+        const uint64_t gr_bits = c.host[4 * i];
         Mem jm{h->has_alloc ? &h->alloc : nullptr, st};
         if (alloc_packed(h, j.nb, j.n, gr_bits, jm) != MPHF_OK) {
-            fail_job(j, MPHF_ENOMEM, mem);
+            fail_job(j, MPHF_ENOMEM, c.mem);
             continue;
         }
         CU(cudaMemsetAsync(h->gr, 0, h->info.gr_words * 8 + 8, st));
         CU(cudaMemsetAsync(h->ef, 0, h->info.ef_words * 8 + 8, st));
         launch_gr_write(h->values, j.node_m, h->node_off, h->bit_pos, j.nb, h->tabs.tau,
                         h->tabs.fixed, h->cum_keys, j.p.leaf_size, j.p.leaf_bijection, h->gr, st);
-        write_ef_dirs(h, j.nb, scan_tmp, st);
+        write_ef_dirs(h, j.nb, c.scan_tmp, st);
         launch_stats(h->values, j.node_m, j.n_nodes, j.p.leaf_size, j.p.leaf_bijection,
                      j.p.tree_shape, j.counters, st);
         CU(cudaGetLastError());
     }
+    std::vector<uint64_t> hc(8 * (jobs.size() ? jobs.size() : 1));
+    for (size_t i = 0; i < jobs.size(); i++)
+        if (!jobs[i]->rc) CU(cudaMemcpyAsync(&hc[8 * i], jobs[i]->counters, 64, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < jobs.size(); i++) {
+        Job &j = *jobs[i];
+        if (j.rc) continue;
+        for (int k = 0; k < 4; k++) {
+            j.h->stats.trials[k] = hc[8 * i + k];
+            j.h->stats.evals[k] = hc[8 * i + 4 + k];
+        }
+    }
+    return MPHF_OK;
+}
+#undef CU
+
+// Default block size of a search: the lower-level nodes of l >= 14 need
+// hundreds of thousands of trials and fill 512 threads; smaller leaves and
+// the fanout-2 tree do better with 256 (B300: l = 8 0.19 vs 0.30 ms, l = 12
+// 15.6 both, fanout-2 l = 24 24.8 vs 28.3 ms; l = 16 8.85 s at 512 threads,
+// two blocks per SM, against 9.22 s with one).
+uint32_t default_threads(const std::vector<Job *> &jobs) {
+    for (const Job *j : jobs)
+        if (!j->rc && j->p.tree_shape == MPHF_TREE_RECSPLIT && j->p.leaf_size >= 14) return 512u;
+    return 256u;
+}
+
+// Runs every job; afterwards each job has rc set and, if rc is OK, h built.
+// Returns a code for failures that affect all jobs (CUDA errors), else OK.
+// All jobs share each phase and ONE persistent search launch over all of
+// their buckets (largest first across jobs).
+int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shared_alloc,
+             uint32_t threads, uint32_t blocks_per_sm) {
+    EngineCtx c{Mem{shared_alloc, st}};
+    std::vector<Job *> jp;
+    uint64_t max_nb = 0, total_slots = 0;
+    for (auto &j : jobs) {
+        jp.push_back(&j);
+        max_nb = j.nb > max_nb ? j.nb : max_nb;
+    }
+    uint32_t *head = nullptr;
+    InstDesc *d_inst = nullptr;
+    WorkItem *items = nullptr;
+    std::vector<InstDesc> hinst;
+    std::vector<uint32_t> inst_job;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t max_m = 0;
+    float ms[4] = {0, 0, 0, 0};
+    int grc = c.reserve(jobs.size(), max_nb);
+    for (auto &e : ev) cudaEventCreate(&e);
+    cudaEventRecord(ev[0], st);
+    head = (uint32_t *)c.mem.get(64);
+    if (grc == MPHF_OK && !head) grc = MPHF_ENOMEM;
+    if (grc == MPHF_OK) grc = c.clear_order();
+    if (grc == MPHF_OK && cudaMemsetAsync(head, 0, 64, st) != cudaSuccess) grc = MPHF_ECUDA;
+    if (grc == MPHF_OK) grc = phase_plan(jp, c);
+    cudaEventRecord(ev[1], st);
+    if (grc == MPHF_OK) {
+        for (Job *j : jp)
+            if (j->planned) total_slots += j->nb;  // every bucket in size_hist gets a slot
+        grc = phase_scatter(jp, c);
+    }
+    if (grc == MPHF_OK) {
+        for (size_t i = 0; i < jp.size(); i++) {
+            if (jp[i]->rc) continue;
+            inst_job.push_back((uint32_t)i);
+            hinst.push_back(jp[i]->desc);
+            max_m = jp[i]->max_m > max_m ? jp[i]->max_m : max_m;
+        }
+        if (total_slots > 0xFFFFFFFFull) grc = MPHF_EINVAL;
+    }
+    if (grc == MPHF_OK && !hinst.empty() && total_slots > 0) {
+        // slots of jobs that failed after their plan stay empty (all-ones: skipped)
+        launch_exclusive_scan(c.size_hist, 4098, c.scan_tmp, st);
+        d_inst = (InstDesc *)c.mem.get(hinst.size() * sizeof(InstDesc));
+        items = (WorkItem *)c.mem.get(total_slots * sizeof(WorkItem));
+        if (!d_inst || !items) {
+            grc = MPHF_ENOMEM;
+        } else if (cudaMemsetAsync(items, 0xFF, total_slots * sizeof(WorkItem), st) != cudaSuccess ||
+                   cudaMemcpyAsync(d_inst, hinst.data(), hinst.size() * sizeof(InstDesc),
+                                   cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            grc = MPHF_ECUDA;
+        } else {
+            for (size_t k = 0; k < inst_job.size(); k++) {
+                Job &j = *jp[inst_job[k]];
+                launch_items_by_size(j.h->cum_keys, j.nb, c.size_hist, c.size_cursor, items,
+                                     (uint32_t)k, st);
+            }
+            if (!threads) threads = default_threads(jp);
+            SearchLaunch L = plan_search_launch(max_m, (uint32_t)total_slots, threads, blocks_per_sm);
+            cudaEventRecord(ev[2], st);
+            launch_search(d_inst, items, (uint32_t)total_slots, head, L, st);
+            if (cudaGetLastError() != cudaSuccess) grc = MPHF_ECUDA;
+        }
+    } else {
+        cudaEventRecord(ev[2], st);
+    }
+    cudaEventRecord(ev[3], st);
+    if (grc == MPHF_OK) grc = phase_pack(jp, c);
     cudaEventRecord(ev[4], st);
-    {
-        std::vector<uint64_t> hc(8 * (J ? J : 1));
-        for (size_t i = 0; i < J; i++)
-            if (!jobs[i].rc) CU(cudaMemcpyAsync(&hc[8 * i], jobs[i].counters, 64, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
+    if (grc == MPHF_OK) {
+        cudaEventSynchronize(ev[4]);
         cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
         cudaEventElapsedTime(&ms[1], ev[2], ev[3]);
         cudaEventElapsedTime(&ms[2], ev[3], ev[4]);
         cudaEventElapsedTime(&ms[3], ev[0], ev[4]);
-        for (size_t i = 0; i < J; i++) {
-            Job &j = jobs[i];
-            if (j.rc) continue;
-            for (int k = 0; k < 4; k++) {
-                j.h->stats.trials[k] = hc[8 * i + k];
-                j.h->stats.evals[k] = hc[8 * i + 4 + k];
-            }
-            j.h->stats.ms_plan = ms[0];
-            j.h->stats.ms_search = ms[1];
-            j.h->stats.ms_pack = ms[2];
-            j.h->stats.ms_total = ms[3];
+        for (Job *j : jp) {
+            if (j->rc) continue;
+            j->h->stats.ms_plan = ms[0];
+            j->h->stats.ms_search = ms[1];
+            j->h->stats.ms_pack = ms[2];
+            j->h->stats.ms_total = ms[3];
         }
     }
-done:
-#undef CU
     cudaStreamSynchronize(st);
     for (auto &j : jobs) {
-        free_job_scratch(j, mem);
-        if (grc != MPHF_OK && j.rc == MPHF_OK) fail_job(j, grc, mem);
+        free_job_scratch(j, c.mem);
+        if (grc != MPHF_OK && j.rc == MPHF_OK) fail_job(j, grc, c.mem);
     }
-    mem.put(scan_tmp);
-    mem.put(size_hist);
-    mem.put(size_cursor);
-    mem.put(head);
-    mem.put(d_inst);
-    mem.put(items);
-    cudaStreamSynchronize(st);
-    if (host) cudaFreeHost(host);
+    c.mem.put(head);
+    c.mem.put(d_inst);
+    c.mem.put(items);
+    c.release();
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
     return grc;
@@ -1462,6 +1546,21 @@ int mphf_load(const void *h_buf, size_t len, const mphf_allocator *allocator, vo
 
 // ---------------------------------------------------------------------------
 // Build server with continuous batching.
+//
+// One serving search kernel (k_serve) stays on the device while there is
+// work and takes buckets from a ring in device memory.  A control thread:
+//   - admits queued requests in arrival order while a request slot and
+//     device memory are free: it runs their fingerprint, bucket sort and plan
+//     on the preparation stream (these kernels run beside the search, on the
+//     SM room the search leaves free) and stages their work items;
+//   - keeps the ring filled, a few items from each running request in turn,
+//     so a request admitted while others are on the device gets blocks
+//     within about one bucket's time;
+//   - polls the per-request bucket counters and packs (Golomb-Rice, Elias-
+//     Fano) each request as soon as its last bucket is done, while the others
+//     keep searching; the request completes on its own, not with a batch.
+// Every request goes through the same kernels as a plain build, so its
+// function is identical.
 namespace {
 
 struct ServerRequest {
@@ -1484,6 +1583,19 @@ uint64_t build_bytes(const mphf_build_desc &d) {
     return 16 * d.n + 48 * nb + (1u << 20);
 }
 
+constexpr uint32_t kRing = 1u << 16;           // work items the ring holds
+constexpr uint32_t kMaxSlots = MPHF_SERVER_MAX_REQUESTS;
+
+// A request on the device.
+struct Active {
+    ServerRequest *r = nullptr;
+    Job job;
+    uint32_t slot = 0;
+    WorkItem *staging = nullptr;  // its buckets' work items, largest first
+    uint64_t nb = 0, published = 0;
+    uint64_t reserve = 0;         // device bytes counted against the budget
+};
+
 }  // namespace
 
 struct mphf_server {
@@ -1494,81 +1606,287 @@ struct mphf_server {
     std::condition_variable cv_work, cv_done;
     std::deque<ServerRequest *> pending;
     std::unordered_map<uint64_t, ServerRequest *> requests;
-    std::vector<std::thread> workers;
-    std::vector<cudaStream_t> streams;
-    uint64_t next_ticket = 1, reserved = 0;
-    uint32_t inflight = 0;
+    std::thread control;
+    uint64_t next_ticket = 1;
     bool stop = false;
+    int fatal = MPHF_OK;  // a CUDA failure of the server itself
+    // device side
+    cudaStream_t prep = nullptr, search = nullptr, poll = nullptr;
+    ServeCtl *ctl = nullptr;
+    WorkItem *ring = nullptr;
+    InstDesc *insts = nullptr;
+    unsigned int *done = nullptr, *sm_count = nullptr;
+    uint64_t *pinned = nullptr;  // [0] new tail, [1] head seen, then done[] as 32-bit words
+    ServeLaunch launch{};
 };
 
-static void server_worker(mphf_server_t *S, int w) {
-    cudaSetDevice(S->device);
-    cudaStream_t st = S->streams[w];
-    std::unique_lock<std::mutex> lk(S->mu);
-    for (;;) {
-        S->cv_work.wait_for(lk, std::chrono::milliseconds(50),
-                            [&] { return S->stop || !S->pending.empty(); });
-        if (S->pending.empty()) {
-            if (S->stop) break;
-            continue;
-        }
-        // admission: pending requests in arrival order while device memory allows
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-            cudaGetLastError();
-            free_b = 0;
-        }
-        int64_t budget = (int64_t)free_b - (int64_t)S->cfg.hbm_reserve_bytes - (int64_t)S->reserved;
-        std::vector<ServerRequest *> batch;
-        uint64_t need = 0;
-        while (!S->pending.empty() && batch.size() < S->cfg.max_batch) {
-            uint64_t b = build_bytes(S->pending.front()->desc);
-            bool fits = (int64_t)(need + b) <= budget;
-            // a request that never fits still runs when nothing else is on the device
-            if (!fits && !(batch.empty() && S->inflight == 0)) break;
-            batch.push_back(S->pending.front());
-            S->pending.pop_front();
-            need += b;
-        }
-        if (batch.empty()) {  // wait for memory to come back
-            S->cv_done.wait_for(lk, std::chrono::milliseconds(20));
-            continue;
-        }
-        S->reserved += need;
-        S->inflight++;
-        const double t_admit = seconds_since(S->t0);
-        for (auto *r : batch) r->t.admitted = t_admit;
-        lk.unlock();
+namespace {
 
-        std::vector<Job> jobs(batch.size());
-        for (size_t i = 0; i < batch.size(); i++) {
-            const mphf_build_desc &d = batch[i]->desc;
+void finish(mphf_server_t *S, ServerRequest *r, int status, mphf_t *h) {
+    std::lock_guard<std::mutex> g(S->mu);
+    r->status = status;
+    r->out = status == MPHF_OK ? h : nullptr;
+    r->t.finished = seconds_since(S->t0);
+    r->done = true;
+    S->cv_done.notify_all();
+}
+
+// Fingerprints, sort, plan and work items of one request on the preparation
+// stream; its descriptor goes to slot a.slot.  Returns a server-wide error
+// (CUDA) or OK; a failure of the request alone is left in a.job.rc.
+int prepare(mphf_server_t *S, EngineCtx &c, Active &a) {
+    Job &j = a.job;
+    std::vector<Job *> jp{&j};
+    int rc = c.reserve(1, j.nb);
+    if (rc != MPHF_OK) return rc;
+    if ((rc = c.clear_order()) != MPHF_OK) return rc;
+    if ((rc = phase_plan(jp, c)) != MPHF_OK) return rc;
+    if (j.rc) return MPHF_OK;
+    if ((rc = phase_scatter(jp, c)) != MPHF_OK) return rc;
+    if (j.rc) return MPHF_OK;
+    a.nb = j.nb;
+    a.staging = (WorkItem *)c.mem.get(j.nb * sizeof(WorkItem) + 8);
+    if (!a.staging) {
+        fail_job(j, MPHF_ENOMEM, c.mem);
+        return MPHF_OK;
+    }
+    const cudaStream_t st = c.mem.st;
+    launch_exclusive_scan(c.size_hist, 4098, c.scan_tmp, st);
+    launch_items_by_size(j.h->cum_keys, j.nb, c.size_hist, c.size_cursor, a.staging, a.slot, st);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(S->insts + a.slot, &j.desc, sizeof(InstDesc), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(S->done + a.slot, 0, sizeof(unsigned int), st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
+    }
+    return MPHF_OK;
+}
+
+// Sets the search's stop flag (copied from pinned memory, then synchronised).
+int set_stop(mphf_server_t *S, uint32_t v) {
+    uint32_t *p = (uint32_t *)S->pinned;
+    p[0] = v;
+    if (cudaMemcpyAsync(&S->ctl->stop, p, 4, cudaMemcpyHostToDevice, S->prep) != cudaSuccess ||
+        cudaStreamSynchronize(S->prep) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
+    }
+    return MPHF_OK;
+}
+
+void release_active(EngineCtx &c, Active &a) {
+    free_job_scratch(a.job, c.mem);
+    c.mem.put(a.staging);
+    a.staging = nullptr;
+}
+
+void server_control(mphf_server_t *S) {
+    cudaSetDevice(S->device);
+    EngineCtx c{Mem{nullptr, S->prep}};
+    std::vector<Active *> active;
+    std::vector<uint32_t> free_slots;
+    for (uint32_t i = S->cfg.max_requests; i-- > 0;) free_slots.push_back(i);
+    uint64_t tail = 0, head = 0;
+    bool running = false;  // a serving search was launched and may still run
+    size_t rr = 0;  // round-robin position over the active requests
+    const uint64_t low_water = 2ull * S->launch.working_blocks;
+    const unsigned long long idle_ns = (unsigned long long)S->cfg.idle_ms * 1000000ull;
+    auto fatal = [&](int rc) {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->fatal == MPHF_OK) S->fatal = rc;
+    };
+    for (;;) {
+        bool progress = false;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->fatal != MPHF_OK) {  // the device failed: every request gets the error
+                const int rc = S->fatal;
+                std::vector<ServerRequest *> left(S->pending.begin(), S->pending.end());
+                S->pending.clear();
+                lk.unlock();
+                for (ServerRequest *r : left) finish(S, r, rc, nullptr);
+                for (Active *a : active) {
+                    if (a->job.h) fail_job(a->job, rc, c.mem);
+                    release_active(c, *a);
+                    finish(S, a->r, rc, nullptr);
+                    delete a;
+                }
+                active.clear();
+                break;
+            }
+        }
+        // 1. admission, in arrival order, while a slot and memory are free
+        for (;;) {
+            ServerRequest *r = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(S->mu);
+                if (S->pending.empty() || free_slots.empty()) break;
+                size_t free_b = 0, total_b = 0;
+                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+                    cudaGetLastError();
+                    free_b = 0;
+                }
+                // memory of admitted requests is already allocated, so free_b counts it
+                const int64_t budget = (int64_t)free_b - (int64_t)S->cfg.hbm_reserve_bytes;
+                const uint64_t need = build_bytes(S->pending.front()->desc);
+                // a request that never fits still runs when nothing else is on the device
+                if ((int64_t)need > budget && !active.empty()) break;
+                r = S->pending.front();
+                S->pending.pop_front();
+                r->t.admitted = seconds_since(S->t0);
+            }
+            progress = true;
+            Active *a = new Active;
+            a->r = r;
+            a->slot = free_slots.back();
+            free_slots.pop_back();
             mphf_build_params p;
             mphf_default_params(&p);
-            p.leaf_size = d.leaf_size;
-            p.bucket_size = d.bucket_size;
-            p.key_bytes = d.key_bytes;
-            p.leaf_bijection = d.leaf_bijection;
-            p.tree_shape = d.tree_shape;
-            p.max_value = d.max_value ? d.max_value : MPHF_DEFAULT_MAX_VALUE;
-            start_job(jobs[i], d.d_keys, d.n, p);
+            p.leaf_size = r->desc.leaf_size;
+            p.bucket_size = r->desc.bucket_size;
+            p.key_bytes = r->desc.key_bytes;
+            p.leaf_bijection = r->desc.leaf_bijection;
+            p.tree_shape = r->desc.tree_shape;
+            p.max_value = r->desc.max_value ? r->desc.max_value : MPHF_DEFAULT_MAX_VALUE;
+            start_job(a->job, r->desc.d_keys, r->desc.n, p);
+            int rc = a->job.rc ? MPHF_OK : prepare(S, c, *a);
+            if (rc != MPHF_OK) fatal(rc);
+            if (rc != MPHF_OK || a->job.rc) {
+                const int st = rc != MPHF_OK ? rc : a->job.rc;
+                if (rc != MPHF_OK && a->job.h) fail_job(a->job, rc, c.mem);
+                release_active(c, *a);
+                free_slots.push_back(a->slot);
+                finish(S, r, st, nullptr);
+                delete a;
+                continue;
+            }
+            active.push_back(a);
         }
-        int grc = run_jobs(jobs, st, nullptr, 0, 0);
-
-        lk.lock();
-        const double t_done = seconds_since(S->t0);
-        for (size_t i = 0; i < batch.size(); i++) {
-            ServerRequest *r = batch[i];
-            r->status = jobs[i].rc ? jobs[i].rc : grc;
-            r->out = r->status == MPHF_OK ? jobs[i].h : nullptr;
-            r->t.finished = t_done;
-            r->done = true;
+        // 2. keep the ring filled: a few items of each request in turn
+        if (!active.empty() && tail - head < low_water) {
+            const uint64_t start = tail;
+            bool any = true;
+            while (tail - head < low_water + 64 && any) {
+                any = false;
+                for (size_t k = 0; k < active.size() && tail - head < low_water + 64; k++) {
+                    Active &a = *active[(rr + k) % active.size()];
+                    if (a.published >= a.nb) continue;
+                    uint64_t take = a.nb - a.published;
+                    take = take > 8 ? 8 : take;
+                    take = take > kRing - (tail % kRing) ? kRing - (tail % kRing) : take;  // no wrap
+                    if (cudaMemcpyAsync(S->ring + tail % kRing, a.staging + a.published,
+                                        take * sizeof(WorkItem), cudaMemcpyDeviceToDevice,
+                                        S->prep) != cudaSuccess)
+                        fatal(MPHF_ECUDA);
+                    a.published += take;
+                    tail += take;
+                    any = true;
+                }
+                rr++;
+            }
+            if (tail != start) {
+                S->pinned[0] = tail;
+                if (cudaMemcpyAsync(&S->ctl->tail, S->pinned, 8, cudaMemcpyHostToDevice, S->prep) !=
+                        cudaSuccess ||
+                    cudaStreamSynchronize(S->prep) != cudaSuccess) {
+                    cudaGetLastError();
+                    fatal(MPHF_ECUDA);
+                }
+                progress = true;
+            }
         }
-        S->reserved -= need;
-        S->inflight--;
-        S->cv_done.notify_all();
+        // 3. the search must be on the device while items wait (its blocks
+        // leave only when told to, or after the idle bound)
+        if (tail > head) {
+            if (running) {
+                const cudaError_t q = cudaStreamQuery(S->search);
+                if (q != cudaSuccess && q != cudaErrorNotReady) fatal(MPHF_ECUDA);
+                cudaGetLastError();  // a search still running is not an error
+                running = q != cudaSuccess;
+            }
+            if (!running) {
+                if (cudaMemsetAsync(S->sm_count, 0, kServeMaxSms * 4, S->search) != cudaSuccess)
+                    fatal(MPHF_ECUDA);
+                launch_serve(S->insts, S->ring, kRing, S->ctl, S->done, S->sm_count,
+                             S->cfg.reserved_sms, idle_ns, S->launch, S->search);
+                if (cudaGetLastError() != cudaSuccess) fatal(MPHF_ECUDA);
+                running = true;
+            }
+        }
+        // 4. poll the queue head and the per-request bucket counters
+        if (!active.empty()) {
+            uint32_t *d32 = (uint32_t *)(S->pinned + 2);
+            if (cudaMemcpyAsync(S->pinned + 1, &S->ctl->head, 8, cudaMemcpyDeviceToHost, S->poll) != cudaSuccess ||
+                cudaMemcpyAsync(d32, S->done, S->cfg.max_requests * 4, cudaMemcpyDeviceToHost, S->poll) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(S->poll) != cudaSuccess) {
+                cudaGetLastError();
+                fatal(MPHF_ECUDA);
+            }
+            head = S->pinned[1] < tail ? S->pinned[1] : tail;
+            // 5. pack every request whose buckets are all done
+            for (size_t k = 0; k < active.size();) {
+                Active &a = *active[k];
+                if (a.published < a.nb || d32[a.slot] < a.nb) {
+                    k++;
+                    continue;
+                }
+                std::vector<Job *> jp{&a.job};
+                int rc = phase_pack(jp, c);
+                if (rc != MPHF_OK) fatal(rc);
+                const int st = rc != MPHF_OK ? rc : a.job.rc;
+                mphf_t *h = a.job.h;
+                release_active(c, a);
+                if (st != MPHF_OK && h) {
+                    if (!a.job.rc) fail_job(a.job, st, c.mem);
+                    h = nullptr;
+                }
+                free_slots.push_back(a.slot);
+                finish(S, a.r, st, h);
+                delete active[k];
+                active.erase(active.begin() + (long)k);
+                progress = true;
+            }
+        }
+        // 6. nothing on the device: the search leaves, so that the next
+        // request's preparation has the whole GPU
+        if (running && active.empty()) {
+            bool idle;
+            {
+                std::lock_guard<std::mutex> g(S->mu);
+                idle = S->pending.empty();
+            }
+            if (idle) {
+                if (set_stop(S, 1) != MPHF_OK || cudaStreamSynchronize(S->search) != cudaSuccess ||
+                    set_stop(S, 0) != MPHF_OK) {
+                    cudaGetLastError();
+                    fatal(MPHF_ECUDA);
+                }
+                running = false;
+                head = tail;  // every published item was claimed and done
+            }
+        }
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop && S->pending.empty() && active.empty()) break;
+            if (!progress) {
+                if (active.empty())
+                    S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+                else
+                    S->cv_work.wait_for(lk, std::chrono::microseconds(300));
+            }
+        }
     }
+    // no work left: the search's blocks leave, then the server's arrays can go
+    set_stop(S, 1);
+    cudaStreamSynchronize(S->search);
+    cudaGetLastError();
+    c.release();
 }
+
+}  // namespace
 
 extern "C" {
 
@@ -1577,33 +1895,52 @@ int mphf_server_create(const mphf_server_cfg *cfg, mphf_server_t **out) {
     *out = nullptr;
     mphf_server_t *S = new (std::nothrow) mphf_server;
     if (!S) return MPHF_ENOMEM;
-    S->cfg.executors = cfg && cfg->executors ? cfg->executors : 2;
-    S->cfg.max_batch = cfg && cfg->max_batch ? cfg->max_batch : 64;
+    S->cfg.max_requests = cfg && cfg->max_requests ? cfg->max_requests : 64;
+    S->cfg.reserved_sms = cfg ? cfg->reserved_sms : 4;
     S->cfg.hbm_reserve_bytes = cfg && cfg->hbm_reserve_bytes ? cfg->hbm_reserve_bytes : (1ull << 30);
-    if (S->cfg.executors > 16) {
+    S->cfg.idle_ms = cfg && cfg->idle_ms ? cfg->idle_ms : 10000;
+    S->cfg.threads = cfg && cfg->threads ? cfg->threads : 512;
+    if (S->cfg.max_requests > kMaxSlots || S->cfg.idle_ms > 600000 || S->cfg.threads % 32 ||
+        S->cfg.threads < 64 || S->cfg.threads > 512) {
         delete S;
         return MPHF_EINVAL;
     }
     S->t0 = std::chrono::steady_clock::now();
-    if (cudaGetDevice(&S->device) != cudaSuccess) {
+    int lo_prio = 0, hi_prio = 0;
+    bool ok = cudaGetDevice(&S->device) == cudaSuccess &&
+              cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&S->prep, cudaStreamNonBlocking, hi_prio) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&S->search, cudaStreamNonBlocking, lo_prio) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S->poll, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&S->ctl, sizeof(ServeCtl)) == cudaSuccess &&
+              cudaMalloc(&S->ring, kRing * sizeof(WorkItem)) == cudaSuccess &&
+              cudaMalloc(&S->insts, kMaxSlots * sizeof(InstDesc)) == cudaSuccess &&
+              cudaMalloc(&S->done, kMaxSlots * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&S->sm_count, kServeMaxSms * sizeof(unsigned int)) == cudaSuccess &&
+              cudaMallocHost(&S->pinned, 8 * (2 + kMaxSlots / 2)) == cudaSuccess &&
+              cudaMemset(S->ctl, 0, sizeof(ServeCtl)) == cudaSuccess &&
+              cudaMemset(S->done, 0, kMaxSlots * sizeof(unsigned int)) == cudaSuccess &&
+              cudaDeviceSynchronize() == cudaSuccess;
+    if (ok) S->launch = plan_serve_launch(S->cfg.threads, S->cfg.reserved_sms);
+    if (ok) {
+        try {
+            S->control = std::thread(server_control, S);
+        } catch (...) {
+            ok = false;
+        }
+    }
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(S->ctl);
+        cudaFree(S->ring);
+        cudaFree(S->insts);
+        cudaFree(S->done);
+        cudaFree(S->sm_count);
+        if (S->pinned) cudaFreeHost(S->pinned);
+        for (cudaStream_t st : {S->prep, S->search, S->poll})
+            if (st) cudaStreamDestroy(st);
         delete S;
         return MPHF_ECUDA;
-    }
-    for (uint32_t w = 0; w < S->cfg.executors; w++) {
-        cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            for (auto x : S->streams) cudaStreamDestroy(x);
-            delete S;
-            return MPHF_ECUDA;
-        }
-        S->streams.push_back(st);
-    }
-    try {
-        for (uint32_t w = 0; w < S->cfg.executors; w++) S->workers.emplace_back(server_worker, S, (int)w);
-    } catch (...) {  // no thread could be started: stop the ones that were
-        mphf_server_destroy(S);
-        return MPHF_ENOMEM;
     }
     *out = S;
     return MPHF_OK;
@@ -1615,9 +1952,9 @@ int mphf_server_submit(mphf_server_t *S, const mphf_build_desc *desc, uint64_t *
     if (!r) return MPHF_ENOMEM;
     r->desc = *desc;
     std::lock_guard<std::mutex> g(S->mu);
-    if (S->stop) {
+    if (S->stop || S->fatal != MPHF_OK) {
         delete r;
-        return MPHF_EBUSY;
+        return S->fatal != MPHF_OK ? S->fatal : MPHF_EBUSY;
     }
     r->ticket = S->next_ticket++;
     r->t.submitted = seconds_since(S->t0);
@@ -1660,8 +1997,14 @@ int mphf_server_destroy(mphf_server_t *S) {
         S->stop = true;
         S->cv_work.notify_all();
     }
-    for (auto &t : S->workers) t.join();
-    for (auto st : S->streams) cudaStreamDestroy(st);
+    if (S->control.joinable()) S->control.join();
+    cudaFree(S->ctl);
+    cudaFree(S->ring);
+    cudaFree(S->insts);
+    cudaFree(S->done);
+    cudaFree(S->sm_count);
+    cudaFreeHost(S->pinned);
+    for (cudaStream_t st : {S->prep, S->search, S->poll}) cudaStreamDestroy(st);
     for (auto &kv : S->requests) {
         if (kv.second->out) mphf_free(kv.second->out);
         delete kv.second;

@@ -352,7 +352,7 @@ struct BlockState {
     uint8_t st_depth[STACK];
     int sp;
     uint32_t nleaves, leaf_next, flags, item;
-    unsigned long long found;
+    unsigned long long found, claim;
     uint32_t cnt[16];
     unsigned long long lut64[16];  // child -> counter increment (last child: 0)
     uint32_t lut32[16];
@@ -1197,13 +1197,15 @@ __device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucke
                                BlockState &S) {
     const uint32_t tid = threadIdx.x, T = blockDim.x;
     const Shape sh = make_shape(LEAF ? (uint32_t)LEAF : d.leaf, d.tree);
-    const uint64_t kbeg = d.bucket_off[bucket];
-    const uint64_t M = d.bucket_off[bucket + 1] - kbeg;
-    const uint64_t nbase = d.node_off[bucket];
+    // a build's arrays are read past L1 (ld.global.cg): a serving search runs
+    // across requests whose arrays may reuse the addresses of earlier ones
+    const uint64_t kbeg = __ldcg(d.bucket_off + bucket);
+    const uint64_t M = __ldcg(d.bucket_off + bucket + 1) - kbeg;
+    const uint64_t nbase = __ldcg(d.node_off + bucket);
     if (M <= 1 || M > 4096) return;  // nothing stored / refused by the plan
     for (uint32_t i = tid; i < M; i += T) {
-        A.lo[i] = d.lo[kbeg + i];
-        A.bb[i] = d.bb[kbeg + i];
+        A.lo[i] = __ldcg(d.lo + kbeg + i);
+        A.bb[i] = __ldcg(d.bb + kbeg + i);
     }
     if (tid == 0) {
         S.sp = 0;
@@ -1283,6 +1285,118 @@ __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, const Wor
             default: process_bucket<0>(d, w.bucket, A, S); break;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The serving search: the same bucket work as k_search, but the work items
+// arrive while it runs.  The host appends items to a ring and then raises
+// ctl->tail; a block claims the next item by advancing ctl->head.  After a
+// bucket, its build's done counter is raised.  A block that finds the ring
+// empty sleeps and looks again; it leaves when the host sets ctl->stop (no
+// request left) or, as a bound on the wait, after idle_ns without work (the
+// host is gone or stalled; ctl->err records it).  The second block that
+// lands on each of the first reserved_sms SMs exits at once, which leaves
+// room there for the preparation and packing kernels of other requests.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ unsigned long long serve_claim(ServeCtl *c, unsigned long long idle_ns) {
+    const unsigned long long t0 = global_ns();
+    for (uint32_t spin = 0; spin < (1u << 22); spin++) {  // bounded: about a minute of sleeps at most
+        const unsigned long long h = atomicAdd(&c->head, 0ull);  // reads at L2, where the host's copies land
+        const unsigned long long t = atomicAdd(&c->tail, 0ull);
+        if (h < t) {
+            if (atomicCAS(&c->head, h, h + 1) == h) return h;
+            continue;
+        }
+        if (atomicAdd(&c->stop, 0u)) return ~0ull;
+        if (global_ns() - t0 > idle_ns) break;
+        __nanosleep(20000);
+    }
+    atomicOr(&c->err, 1u);  // waited the limit: leave, the host relaunches if work remains
+    return ~0ull;
+}
+
+__device__ __forceinline__ InstDesc load_desc(const InstDesc *p) {
+    static_assert(sizeof(InstDesc) % 8 == 0, "descriptor is copied as 64-bit words");
+    InstDesc d;
+    const unsigned long long *src = (const unsigned long long *)p;
+    unsigned long long *dst = (unsigned long long *)&d;
+#pragma unroll
+    for (uint32_t i = 0; i < sizeof(InstDesc) / 8; i++) dst[i] = __ldcg(src + i);
+    return d;
+}
+
+__global__ void __launch_bounds__(512) k_serve(const InstDesc *insts, const WorkItem *ring,
+                                               uint32_t ring_cap, ServeCtl *ctl, unsigned int *done,
+                                               unsigned int *sm_count, uint32_t reserved_sms,
+                                               unsigned long long idle_ns, uint32_t cap) {
+    extern __shared__ __align__(16) uint8_t dyn[];
+    __shared__ BlockState S;
+    const SmemLayout lay(cap);
+    SmemArrays A;
+    A.lo = (uint64_t *)dyn;
+    A.tlo = A.lo + lay.P;
+    A.bb = dyn + 16u * lay.P;
+    A.tbb = A.bb + lay.P;
+    A.leaf_off = (uint16_t *)(dyn + 18u * lay.P);
+    A.leaf_pidx = A.leaf_off + lay.nl;
+    A.leaf_m = (uint8_t *)(A.leaf_pidx + lay.nl);
+    if (threadIdx.x == 0) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        const uint32_t before = atomicAdd(&sm_count[smid & (kServeMaxSms - 1)], 1u);
+        S.item = smid < reserved_sms && before >= 1;
+    }
+    __syncthreads();
+    if (S.item) return;
+    for (;;) {
+        if (threadIdx.x == 0) S.claim = serve_claim(ctl, idle_ns);
+        __syncthreads();
+        const unsigned long long it = S.claim;
+        __syncthreads();
+        if (it == ~0ull) break;
+        const unsigned long long raw = __ldcg((const unsigned long long *)(ring + it % ring_cap));
+        const WorkItem w{(uint32_t)raw, (uint32_t)(raw >> 32)};
+        const InstDesc d = load_desc(insts + w.inst);
+        switch (d.leaf) {
+            case 8: process_bucket<8>(d, w.bucket, A, S); break;
+            case 12: process_bucket<12>(d, w.bucket, A, S); break;
+            case 16: process_bucket<16>(d, w.bucket, A, S); break;
+            default: process_bucket<0>(d, w.bucket, A, S); break;
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();  // the bucket's values before its completion
+            atomicAdd(&done[w.inst], 1u);
+        }
+    }
+}
+
+ServeLaunch plan_serve_launch(uint32_t threads, uint32_t reserved_sms) {
+    ServeLaunch L;
+    L.cap = 4096;  // any bucket a build accepts
+    L.threads = threads ? threads : 512;
+    L.smem_bytes = SmemLayout(L.cap).bytes;
+    int dev = 0, sms = 148, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_serve, L.threads, L.smem_bytes);
+    if (occ < 1) occ = 1;
+    L.blocks = (uint32_t)sms * (uint32_t)occ;
+    L.working_blocks = L.blocks - (occ > 1 ? (reserved_sms < (uint32_t)sms ? reserved_sms : sms) : 0);
+    return L;
+}
+
+void launch_serve(const InstDesc *insts, const WorkItem *ring, uint32_t ring_cap, ServeCtl *ctl,
+                  unsigned int *done, unsigned int *sm_count, uint32_t reserved_sms,
+                  unsigned long long idle_ns, const ServeLaunch &L, cudaStream_t st) {
+    k_serve<<<L.blocks, L.threads, L.smem_bytes, st>>>(insts, ring, ring_cap, ctl, done, sm_count,
+                                                       reserved_sms, idle_ns, L.cap);
+    note_launches(1);
 }
 
 static uint32_t search_smem(uint32_t cap) { return SmemLayout(cap).bytes; }

@@ -49,6 +49,20 @@ struct SearchLaunch {
     uint32_t cap;            // largest bucket the blocks hold
 };
 
+// The serving search's queue: items [head, tail) of the ring are published
+// and not yet claimed; stop asks idle blocks to leave; err records a block
+// that gave up waiting on a contended claim.
+struct ServeCtl {
+    unsigned long long head, tail;
+    unsigned int stop, err;
+};
+constexpr uint32_t kServeMaxSms = 1024;  // entries of the per-SM block counter (power of two)
+
+struct ServeLaunch {
+    uint32_t threads, blocks, smem_bytes, cap;
+    uint32_t working_blocks;  // blocks left after the reserved SMs' second blocks exit
+};
+
 // Kernels launched by this library in this process (every launcher adds its count).
 void note_launches(uint64_t k);
 uint64_t launches_total();
@@ -83,6 +97,11 @@ void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads, uint32_t blocks_per_sm);
 void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
                    const SearchLaunch &L, cudaStream_t st);
+// The serving search (reads work from a ring the host appends to; see k_serve).
+ServeLaunch plan_serve_launch(uint32_t threads, uint32_t reserved_sms);
+void launch_serve(const InstDesc *insts, const WorkItem *ring, uint32_t ring_cap, ServeCtl *ctl,
+                  unsigned int *done, unsigned int *sm_count, uint32_t reserved_sms,
+                  unsigned long long idle_ns, const ServeLaunch &L, cudaStream_t st);
 // Golomb-Rice coding of the stored values (a ShockHash leaf codes its seed
 // and appends its retrieval vector to the fixed part).
 void launch_gr_lengths(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,

@@ -117,8 +117,9 @@ class Stats(ctypes.Structure):
 
 
 class ServerCfg(ctypes.Structure):
-    _fields_ = [("executors", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
-                ("hbm_reserve_bytes", ctypes.c_uint64)]
+    _fields_ = [("max_requests", ctypes.c_uint32), ("reserved_sms", ctypes.c_uint32),
+                ("hbm_reserve_bytes", ctypes.c_uint64), ("idle_ms", ctypes.c_uint32),
+                ("threads", ctypes.c_uint32)]
 
 
 class RequestTimes(ctypes.Structure):
@@ -456,11 +457,13 @@ def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation=True,
 
 
 class Server:
-    """Build server with continuous batching (mphf_server_*)."""
+    """Build server with continuous batching (mphf_server_*): requests join one
+    serving search on the device and complete one by one."""
 
-    def __init__(self, executors: int = 2, max_batch: int = 64, hbm_reserve_bytes: int = 0):
+    def __init__(self, max_requests: int = 64, reserved_sms: int = 4, hbm_reserve_bytes: int = 0,
+                 idle_ms: int = 0, threads: int = 0):
         _torch()
-        cfg = ServerCfg(executors, max_batch, hbm_reserve_bytes)
+        cfg = ServerCfg(max_requests, reserved_sms, hbm_reserve_bytes, idle_ms, threads)
         h = ctypes.c_void_p()
         _check(lib().mphf_server_create(ctypes.byref(cfg), ctypes.byref(h)), "mphf_server_create")
         self._h = h

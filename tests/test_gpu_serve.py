@@ -59,7 +59,7 @@ def poll_all(srv, tickets, timeout_s=300):
 
 def test_served_results_equal_plain_builds(torch):
     reqs = requests(torch, 16, 31)
-    srv = M.Server(executors=2, max_batch=8)
+    srv = M.Server(max_requests=8)
     tickets = []
 
     def arrive():  # staggered arrivals while earlier requests are on the device
@@ -83,11 +83,11 @@ def test_served_results_equal_plain_builds(torch):
 def test_alone_equals_in_mix(torch):
     reqs = requests(torch, 8, 32)
     probe_keys, probe_leaf = reqs[3]
-    alone = M.Server(executors=1, max_batch=1)
+    alone = M.Server(max_requests=1)
     t = alone.submit(probe_keys, probe_leaf, 500)
     st, a, _ = poll_all(alone, [t])[t]
     alone.close()
-    mix = M.Server(executors=2, max_batch=64)
+    mix = M.Server(max_requests=64)
     tickets = [mix.submit(dk, leaf, 500) for dk, leaf in reqs]
     res = poll_all(mix, tickets)
     st2, b, _ = res[tickets[3]]
@@ -100,7 +100,7 @@ def test_fifo_admission_under_a_memory_budget(torch):
     free, _ = torch.cuda.mem_get_info()
     reqs = requests(torch, 6, 33)
     # reserve almost all free memory: only one request is admitted at a time
-    srv = M.Server(executors=2, max_batch=64, hbm_reserve_bytes=max(free - (64 << 20), 1))
+    srv = M.Server(max_requests=64, hbm_reserve_bytes=max(free - (64 << 20), 1))
     tickets = [srv.submit(dk, leaf, 500) for dk, leaf in reqs]
     res = poll_all(srv, tickets)
     admitted = [res[t][2][1] for t in tickets]
@@ -111,7 +111,7 @@ def test_fifo_admission_under_a_memory_budget(torch):
 
 def test_timeout_and_bad_requests(torch):
     keys = dev(torch, W.distinct_u64(300_000, 34))
-    srv = M.Server(executors=1)
+    srv = M.Server(max_requests=4)
     t_big = srv.submit(keys, 16, 2000)
     assert srv.poll(t_big, 0) is None  # still running: reported, not waited on
     t_bad = srv.submit(keys, 1, 2000)  # leaf size out of range
@@ -125,7 +125,7 @@ def test_timeout_and_bad_requests(torch):
 
 def test_destroy_with_queued_requests(torch):
     reqs = requests(torch, 6, 35)
-    srv = M.Server(executors=1, max_batch=2)
+    srv = M.Server(max_requests=2)
     for dk, leaf in reqs:
         srv.submit(dk, leaf, 500)
     srv.close()  # finishes the queue, frees unpolled results
@@ -137,7 +137,7 @@ def test_served_shockhash_and_fanout2_requests(torch, orc):
     specs = [(12000, 24, M.SHOCKHASH, M.TREE_FANOUT2), (8000, 16, M.SHOCKHASH, M.TREE_RECSPLIT),
              (9000, 12, M.ROTATION, M.TREE_RECSPLIT), (7000, 8, M.ROTATION, M.TREE_FANOUT2)]
     keys = [dev(torch, W.distinct_u64(n, 5200 + i)) for i, (n, *_r) in enumerate(specs)]
-    srv = M.Server(executors=2, max_batch=8)
+    srv = M.Server(max_requests=8)
     try:
         tickets = [srv.submit(k, leaf, 2000, bij, tree=tree)
                    for k, (n, leaf, bij, tree) in zip(keys, specs)]
@@ -149,5 +149,52 @@ def test_served_shockhash_and_fanout2_requests(torch, orc):
             same(built, alone)
             assert built.info.tree_shape == tree and built.info.leaf_bijection == bij
             assert built.verify(k) == 0
+    finally:
+        srv.close()
+
+
+def test_requests_join_a_running_search(torch):
+    """A long request is on the device; short ones that arrive later are
+    admitted while it runs, share the serving search with it and finish
+    before it, each identical to its plain build."""
+    big = dev(torch, W.distinct_u64(1_500_000, 36))
+    small = [dev(torch, W.distinct_u64(20_000 + 5000 * i, 37 + i)) for i in range(4)]
+    srv = M.Server(max_requests=64)
+    try:
+        t_big = srv.submit(big, 16, 2000)
+        time.sleep(0.3)
+        ts = [srv.submit(k, 12 if i % 2 else 8, 1000) for i, k in enumerate(small)]
+        res = poll_all(srv, [t_big] + ts)
+        big_done = res[t_big][2][2]
+        for t, k, i in zip(ts, small, range(4)):
+            st, built, (sub, adm, fin) = res[t]
+            assert st == M.OK
+            assert adm < big_done and fin < big_done, (adm, fin, big_done)
+            same(built, M.MPHF.build(k, 12 if i % 2 else 8, 1000, True))
+        assert res[t_big][0] == M.OK
+        same(res[t_big][1], M.MPHF.build(big, 16, 2000, True))
+    finally:
+        srv.close()
+
+
+def test_freed_request_slots_are_refilled(torch):
+    """With room for two requests, the short ones take turns in the second
+    slot while the long one keeps the first: each is admitted when the one
+    before it finishes, all before the long request is done."""
+    big = dev(torch, W.distinct_u64(1_200_000, 38))
+    small = [dev(torch, W.distinct_u64(30_000, 39 + i)) for i in range(3)]
+    srv = M.Server(max_requests=2)
+    try:
+        t_big = srv.submit(big, 16, 2000)
+        ts = [srv.submit(k, 8, 1000) for k in small]
+        res = poll_all(srv, [t_big] + ts)
+        big_done = res[t_big][2][2]
+        times = [res[t][2] for t in ts]
+        for (sub, adm, fin) in times:
+            assert fin < big_done
+        for prev, nxt in zip(times, times[1:]):
+            assert nxt[1] >= prev[2] - 1e-3  # admitted once the previous one freed its slot
+        for t, k in zip(ts, small):
+            same(res[t][1], M.MPHF.build(k, 8, 1000, True))
     finally:
         srv.close()
