@@ -229,7 +229,7 @@ def batch_vs_plain(M, torch, count: int, hi_exp: float = 5.0) -> dict:
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     t0 = time.perf_counter()
-    plain = [M.MPHF.build(k, l, 2000, True) for k, l in zip(keys, leaves)]
+    plain = [M.MPHF.build(k, l, 2000, True, tuned=True) for k, l in zip(keys, leaves)]
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     identical = all(same_function(a, b) for a, b in zip(batched, plain))
@@ -472,11 +472,18 @@ def run_ours(args):
 
     from paper_2212_09562_b300 import shard as S
 
+    # launch shape and seeds per thread from the autotuner (tuned now if this
+    # device has no cached choice for the workload's leaf size)
+    from paper_2212_09562_b300 import autotune as A
+    if A.tuned(w.leaf, w.rotation, w.tree) == A.DEFAULT:
+        A.tune(w.leaf, w.rotation, bucket=w.bucket, tree=w.tree)
+    shape = A.tuned(w.leaf, w.rotation, w.tree)
+
     def one_build(k):
         """(function, the part this rank searched): the whole build on one GPU,
         else one function over all ranks' keys in bucket-range shards."""
         if world == 1:
-            g = M.MPHF.build(k, w.leaf, w.bucket, w.rotation, tree=w.tree)
+            g = M.MPHF.build(k, w.leaf, w.bucket, w.rotation, tree=w.tree, tuned=True)
             return g, g
         return S.build_sharded(k, w.leaf, w.bucket, w.rotation, tree=w.tree)
 
@@ -558,6 +565,9 @@ def run_ours(args):
                       "tree": "fanout 2" if w.tree else "lower aggregation levels",
                       "key_bytes": w.key_bytes,
                       "l2": "flushed between steps (256 MB write)",
+                      "search_shape": {"threads_per_block": shape[0], "blocks_per_sm": shape[1],
+                                       "seeds_per_thread": shape[2],
+                                       "source": "autotuner (0 = library default)"},
                       "parallelism": ("1 GPU" if world == 1 else
                                       f"{world} GPUs: one function of {world} x {w.n} keys in "
                                       "bucket-range shards (all-to-all of keys, all-gather of shards)")},

@@ -49,6 +49,8 @@ extern "C" {
 #define MPHF_EBUCKET (-7)        /* a bucket holds more than MPHF_MAX_BUCKET keys            */
 #define MPHF_ENOTIMPL (-8)       /* not supported by this build of the library               */
 #define MPHF_ETIMEOUT (-9)       /* a bounded device wait gave up                            */
+#define MPHF_ECAPACITY (-10)     /* a prepared build's packed function outgrew the space
+                                    reserved for it (build it with mphf_build_ex instead)    */
 
 #define MPHF_MAX_BUCKET 4096u    /* largest bucket a build accepts (keys)                    */
 #define MPHF_MAX_LEAF 24u        /* leaf sizes 2..24                                          */
@@ -89,6 +91,11 @@ typedef struct {
  *                    2.2, "Splitting Trees"); MPHF_TREE_FANOUT2: fanout 2 for
  *                    the entire tree, each left part a multiple of l (the
  *                    configuration Appendix C uses with ShockHash leaves).
+ *   seeds_per_thread seeds each thread tests per round in the split search of
+ *                    full lower-level nodes (each key load feeds that many
+ *                    independent hash chains): 1, 2 or 4; 0 = the default
+ *                    (2 for l >= 16, else 1).  The result does not depend on
+ *                    it; the autotuner picks it per device and leaf size.
  *   leaf_method      how plain and rotation leaves are searched (same result
  *                    every time; ShockHash leaves have one search):
  *                    MPHF_LEAF_LOCKSTEP  every trial hashes all m keys
@@ -120,6 +127,8 @@ typedef struct {
     uint32_t blocks_per_sm;
     uint32_t leaf_method;
     uint32_t tree_shape;
+    uint32_t seeds_per_thread;
+    uint32_t reserved;           /* 0 */
 } mphf_build_params;
 
 /* Sizes and parameters of a built function. */
@@ -180,6 +189,39 @@ int mphf_build_ex(const void *d_keys, uint64_t n, const mphf_build_params *param
  * The parameters and n are checked before anything is allocated or copied. */
 int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *params,
                     void *stream, mphf_t **out);
+
+/* ---------------------------------------------------------------------------
+ * A build in three calls, whose device work can be captured once in a CUDA
+ * graph and replayed on new keys (the paper has no counterpart).  A plain
+ * build reads its node count and code length back to the host to size its
+ * outputs; a prepared build reserves upper bounds instead (n values, and
+ * gr_capacity_bits of Golomb-Rice code: 0 = 16 bits per key + 128 per bucket
+ * + 4096, about ten times what any leaf method needs), so enqueueing it
+ * involves no allocation and no host synchronisation.  The stored words are
+ * those of mphf_build_ex on the same keys. */
+
+/* Allocates a build of exactly n keys (1 <= n < 2^32) with params (as for
+ * mphf_build_ex) on the current device, through params->allocator if given.
+ * *out is not a usable function until mphf_build_finish succeeds.  Errors:
+ * MPHF_EINVAL (bad parameters or n = 0), MPHF_ENOMEM, MPHF_ECUDA.
+ * Synchronises the device. */
+int mphf_build_prepare(uint64_t n, const mphf_build_params *params, uint64_t gr_capacity_bits,
+                       mphf_t **out);
+
+/* Issues the whole build of the n keys at d_keys (device, 8-byte aligned,
+ * key_bytes each) on the stream: memsets and kernels only, so it may run
+ * inside stream capture; a captured graph rebuilds from whatever keys are at
+ * d_keys when it is launched.  The previous contents of h are overwritten.
+ * MPHF_EINVAL for a handle not made by mphf_build_prepare, a bad pointer or
+ * another device current than h's. */
+int mphf_build_enqueue(mphf_t *h, const void *d_keys, void *stream);
+
+/* Waits for the stream, then reads the build's status and totals back and
+ * makes h a usable function.  Returns the build's error, if any
+ * (MPHF_EDUPLICATE, MPHF_EBUCKET, MPHF_ESEARCH_LIMIT, or MPHF_ECAPACITY when
+ * the code outgrew gr_capacity_bits), in which case h stays unusable until
+ * the next successful enqueue and finish. */
+int mphf_build_finish(mphf_t *h, void *stream);
 
 /* ---------------------------------------------------------------------------
  * One function built on several GPUs (Section 5.2, "Multi-Threading": each
@@ -356,7 +398,7 @@ typedef struct {
     uint32_t leaf_bijection;  /* MPHF_BIJECTION_* */
     uint64_t max_value;       /* 0 = MPHF_DEFAULT_MAX_VALUE */
     uint32_t tree_shape;      /* MPHF_TREE_* */
-    uint32_t reserved;        /* 0 */
+    uint32_t seeds_per_thread; /* as in mphf_build_params (0 = default) */
 } mphf_build_desc;
 
 int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream, mphf_t **outs,

@@ -1,12 +1,12 @@
-"""Launch-shape autotuner for the search kernel.
+"""Autotuner for the search kernel: launch shape and seeds per thread.
 
 For one leaf size and leaf method it builds a representative key set once per
-candidate launch shape (threads per block, resident blocks per SM), times the
-search kernel with the library's own CUDA events, checks that every candidate
-produced the same function, and keeps the fastest.  Results are cached per
-device name in a JSON file (``MPHF_TUNE_CACHE``, default
-``~/.cache/mphf_tune.json``); ``tuned(leaf, rotation)`` returns the cached
-shape or the library default.
+candidate (threads per block, resident blocks per SM, seeds per thread of the
+full lower-level split searches), times the search kernel with the library's
+own CUDA events, checks that every candidate produced the same function, and
+keeps the fastest.  Results are cached per device name in a JSON file
+(``MPHF_TUNE_CACHE``, default ``~/.cache/mphf_tune.json``);
+``tuned(leaf, rotation)`` returns the cached choice or the library default.
 
     python -m paper_2212_09562_b300.autotune 8 12 16
 """
@@ -15,14 +15,18 @@ from __future__ import annotations
 import json
 import os
 import sys
+import time
 
 import numpy as np
 
 from . import mphf as M
 from . import workloads as W
 
-CANDIDATES = [(128, 0), (256, 0), (512, 0), (256, 2), (512, 1)]
-DEFAULT = (0, 0)  # library default (512 or 256 threads by tree and leaf size, as many blocks as fit)
+# (threads per block, blocks per SM, seeds per thread); 0 = the library's default
+CANDIDATES = [(128, 0, 1), (256, 0, 1), (256, 0, 2), (512, 0, 1), (512, 0, 2), (512, 0, 4),
+              (256, 2, 2), (512, 1, 2)]
+DEFAULT = (0, 0, 0)  # library default (512 or 256 threads by tree and leaf size, as many
+                     # blocks as fit, 2 seeds per thread at l >= 16, else 1)
 
 
 def cache_path() -> str:
@@ -49,35 +53,48 @@ def _key(leaf: int, rotation, tree: int = M.TREE_RECSPLIT) -> str:
     return k if tree == M.TREE_RECSPLIT else f"{k}|tree={int(tree)}"
 
 
-def tuned(leaf: int, rotation: bool = True, tree: int = M.TREE_RECSPLIT) -> tuple[int, int]:
-    """(threads_per_block, blocks_per_sm) from the cache, else the library default."""
+def tuned(leaf: int, rotation: bool = True, tree: int = M.TREE_RECSPLIT) -> tuple[int, int, int]:
+    """(threads_per_block, blocks_per_sm, seeds_per_thread) from the cache, else
+    the library default."""
     entry = _load().get(_key(leaf, rotation, tree))
-    return (int(entry["threads"]), int(entry["blocks_per_sm"])) if entry else DEFAULT
+    if not entry:
+        return DEFAULT
+    return int(entry["threads"]), int(entry["blocks_per_sm"]), int(entry.get("seeds_per_thread", 0))
 
 
 def tune(leaf: int, rotation: bool = True, n: int | None = None, bucket: int = 2000,
-         candidates=CANDIDATES, save: bool = True, tree: int = M.TREE_RECSPLIT) -> dict:
-    """Times every candidate shape on one build of n keys; returns the result record."""
+         candidates=CANDIDATES, save: bool = True, tree: int = M.TREE_RECSPLIT,
+         warm_s: float = 3.0) -> dict:
+    """Times every candidate on builds of n keys (each twice, in opposite orders,
+    after warm_s seconds of warm-up builds); returns the result record."""
     import torch
     if n is None:  # 1500 buckets of 2000 keys: five waves at the default shape, so the tail
         n = 3_000_000  # of the last wave does not decide (at 300 buckets it did)
     keys = torch.from_numpy(W.distinct_u64(n, 4711 + leaf).view(np.int64)).cuda()
-    M.MPHF.build(keys[: min(n, 20_000)], leaf, bucket, rotation, tree=tree).close()  # warm-up
+    # warm-up: the SM clock of an idle GPU ramps up over the first seconds of
+    # load, which would favour the candidates timed last
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < warm_s:
+        M.MPHF.build(keys, leaf, bucket, rotation, tree=tree).close()
+        torch.cuda.synchronize()
     times, ref = {}, None
-    for threads, blocks in candidates:
-        g = M.MPHF.build(keys, leaf, bucket, rotation, threads_per_block=threads,
-                         blocks_per_sm=blocks, tree=tree)
-        values = g.host_arrays()["values"]
-        if ref is None:
-            ref = values
-        elif not np.array_equal(values, ref):
-            raise RuntimeError(f"launch shape {(threads, blocks)} changed the result")
-        times[(threads, blocks)] = g.stats()["ms"]["search"]
-        g.close()
+    for order in (list(candidates), list(reversed(candidates))):  # two passes, best of both
+        for threads, blocks, spt in order:
+            g = M.MPHF.build(keys, leaf, bucket, rotation, threads_per_block=threads,
+                             blocks_per_sm=blocks, tree=tree, seeds_per_thread=spt)
+            values = g.host_arrays()["values"]
+            if ref is None:
+                ref = values
+            elif not np.array_equal(values, ref):
+                raise RuntimeError(f"candidate {(threads, blocks, spt)} changed the result")
+            ms = g.stats()["ms"]["search"]
+            key = (threads, blocks, spt)
+            times[key] = min(ms, times.get(key, ms))
+            g.close()
     best = min(times, key=times.get)
-    rec = {"threads": best[0], "blocks_per_sm": best[1], "search_ms": times[best], "n": n,
-           "bucket": bucket,
-           "candidates": {f"{t}x{b}": ms for (t, b), ms in sorted(times.items())}}
+    rec = {"threads": best[0], "blocks_per_sm": best[1], "seeds_per_thread": best[2],
+           "search_ms": times[best], "n": n, "bucket": bucket,
+           "candidates": {f"{t}x{b}x{s}": ms for (t, b, s), ms in sorted(times.items())}}
     if save:
         data = _load()
         data[_key(leaf, rotation, tree)] = rec

@@ -26,20 +26,12 @@
 #include "common.cuh"
 #include "engine.h"
 #include "mphf.h"
+#include "handle.h"
 #include "tables.h"
 
 using namespace rs;
 
-namespace {
-
-struct DevTables {
-    uint8_t *tau = nullptr;
-    uint32_t *nodes = nullptr;
-    uint32_t *fixed = nullptr;
-    uint16_t *left = nullptr;
-    uint32_t *mod_c = nullptr;
-    uint64_t *mod_M = nullptr;
-};
+namespace rs {
 
 // Per-device copy of the exact-remainder constants per node size.
 int device_mod_tables(int dev, uint32_t **c, uint64_t **M) {
@@ -156,85 +148,22 @@ int device_rot_tables(int dev, const uint8_t **canon, const uint8_t **period) {
     return MPHF_OK;
 }
 
-struct Mem {
-    const mphf_allocator *a;
-    cudaStream_t st;
-    void *get(size_t bytes) {
-        if (bytes == 0) bytes = 8;
-        if (a) return a->alloc(bytes, st, a->ctx);
-        void *p = nullptr;
-        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        return p;
-    }
-    void put(void *p) {
-        if (!p) return;
-        if (a)
-            a->free(p, st, a->ctx);
-        else
-            cudaFreeAsync(p, st);
-    }
-};
-
-struct EfDims {
-    uint32_t L;
-    uint64_t low_words, high_words;
-};
-
-EfDims ef_dims(uint64_t k, uint64_t last) {
-    EfDims d;
-    d.L = 0;
-    if (last >= k) {
-        uint64_t q = last / k;
-        while (q >>= 1) d.L++;
-    }
-    d.low_words = (k * d.L + 63) / 64;
-    d.high_words = ((last >> d.L) + k + 63) / 64;
-    return d;
-}
-
 // Serialised form: a header of kHeadWords words starting with kMagic (the
 // bytes "RMPFPH01" read as a little-endian word), then the Golomb-Rice and
 // Elias-Fano words.
 constexpr size_t kHeadWords = 16;
 constexpr uint64_t kMagic = 0x3130485046504D52ull;
 
-int status_code(uint32_t st) {
-    if (st & ST_RANGE) return MPHF_EINVAL;  // a shard was given a key of another shard
-    if (st & ST_BUCKET) return MPHF_EBUCKET;
-    if (st & ST_DUPLICATE) return MPHF_EDUPLICATE;
-    if (st & ST_LIMIT) return MPHF_ESEARCH_LIMIT;
-    if (st & ST_TIMEOUT) return MPHF_ETIMEOUT;
-    return MPHF_OK;
-}
 
 
-}  // namespace
-
-struct mphf {
-    int device = 0;
-    mphf_info info{};
-    mphf_allocator alloc{};
-    bool has_alloc = false;
-    uint64_t *values = nullptr, *node_off = nullptr, *cum_keys = nullptr, *bit_pos = nullptr;
-    uint64_t *gr = nullptr, *ef = nullptr, *ef_dir = nullptr;  // ef_dir: rank then select directories
-    uint64_t ef_dir_len[2] = {0, 0};
-    uint64_t ef_sel_len = 0;
-    DevTables tabs;
-    mphf_stats stats{};
-    // a shard: buckets [b_lo, b_lo + info.nb) of a function over n_total keys
-    // hashed to nb_hash buckets (not queryable on its own)
-    bool shard = false;
-    uint64_t b_lo = 0, nb_hash = 0, n_total = 0;
-};
+}  // namespace rs
 
 // Frees a handle's arrays in the order of stream st (the build's stream while
 // a build fails; the legacy stream after a device synchronisation otherwise).
-static void release(mphf_t *h, cudaStream_t st) {
+void rs::release(mphf_t *h, cudaStream_t st) {
     if (!h) return;
     Mem mem{h->has_alloc ? &h->alloc : nullptr, st};
+    release_plan(h, mem);
     void *ptrs[] = {h->values, h->node_off, h->cum_keys, h->bit_pos, h->gr, h->ef, h->ef_dir};
     for (void *p : ptrs) mem.put(p);
     delete h;
@@ -243,7 +172,7 @@ static void release(mphf_t *h, cudaStream_t st) {
 // Sizes of the packed function (Golomb-Rice words, the two Elias-Fano
 // sequences over nb + 1 bucket offsets, their rank and select directories)
 // and its arrays from the handle's allocator.  Nothing is written yet.
-static int alloc_packed(mphf_t *h, uint64_t nb, uint64_t n, uint64_t gr_bits, Mem &jm) {
+int rs::alloc_packed(mphf_t *h, uint64_t nb, uint64_t n, uint64_t gr_bits, Mem &jm) {
     h->info.gr_bits = gr_bits;
     h->info.gr_words = (gr_bits + 63) / 64;
     EfDims e0 = ef_dims(nb + 1, n), e1 = ef_dims(nb + 1, gr_bits);
@@ -265,7 +194,7 @@ static int alloc_packed(mphf_t *h, uint64_t nb, uint64_t n, uint64_t gr_bits, Me
 
 // Elias-Fano sequences of the key and bit offsets (Section 2.2,
 // "Representation") into the zeroed h->ef, and their query directories.
-static void write_ef_dirs(mphf_t *h, uint64_t nb, uint64_t *scan_tmp, cudaStream_t st) {
+void rs::write_ef_dirs(mphf_t *h, uint64_t nb, uint64_t *scan_tmp, cudaStream_t st) {
     const mphf_info &I = h->info;
     uint64_t *lo0 = h->ef, *hi0 = lo0 + I.ef_seq_words[0], *lo1 = hi0 + I.ef_seq_words[1],
              *hi1 = lo1 + I.ef_seq_words[2];
@@ -304,6 +233,7 @@ const char *mphf_strerror(int code) {
         case MPHF_EBUCKET: return "a bucket holds more than 4096 keys";
         case MPHF_ENOTIMPL: return "not implemented";
         case MPHF_ETIMEOUT: return "a bounded device wait timed out";
+        case MPHF_ECAPACITY: return "the packed function outgrew the space reserved for the prepared build";
         default: return "unknown error";
     }
 }
@@ -359,6 +289,9 @@ int check_shape(uint64_t n, const mphf_build_params *p) {
         return MPHF_EINVAL;
     if (p->leaf_method > MPHF_LEAF_TABLE || p->leaf_bijection > MPHF_BIJECTION_SHOCKHASH ||
         p->tree_shape > MPHF_TREE_FANOUT2)
+        return MPHF_EINVAL;
+    if (p->seeds_per_thread != 0 && p->seeds_per_thread != 1 && p->seeds_per_thread != 2 &&
+        p->seeds_per_thread != 4)
         return MPHF_EINVAL;
     return MPHF_OK;
 }
@@ -557,6 +490,7 @@ int phase_scatter(std::vector<Job *> &jobs, EngineCtx &c) {
         d.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
         d.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
         d.leaf_method = j.p.leaf_method;
+        d.spt = j.p.seeds_per_thread ? j.p.seeds_per_thread : (j.p.leaf_size >= 16 ? 2u : 1u);
         d.mod_c = h->tabs.mod_c;
         d.mod_M = h->tabs.mod_M;
         d.rot_canon = d.rot_period = nullptr;
@@ -1123,7 +1057,7 @@ static int query_args(const mphf_t *h, const void *d_keys, uint64_t n) {
         cudaGetLastError();
         return MPHF_ECUDA;
     }
-    if (dev != h->device || h->info.n == 0 || h->shard) return MPHF_EINVAL;
+    if (dev != h->device || h->info.n == 0 || h->shard || !h->ready) return MPHF_EINVAL;
     return MPHF_OK;
 }
 
@@ -1204,7 +1138,7 @@ int mphf_get_stats(const mphf_t *h, mphf_stats *s) {
 }
 
 int mphf_serialize(const mphf_t *h, void *h_buf, size_t *len, void *stream) {
-    if (!h || !len || h->shard) return MPHF_EINVAL;
+    if (!h || !len || h->shard || !h->ready) return MPHF_EINVAL;
     const size_t head = sizeof(uint64_t) * kHeadWords;
     const size_t need = head + (h->info.gr_words + h->info.ef_words) * 8;
     if (!h_buf) {
@@ -1264,6 +1198,7 @@ int mphf_build_batch(const mphf_build_desc *descs, uint32_t count, void *stream,
         p.leaf_bijection = descs[i].leaf_bijection;
         p.tree_shape = descs[i].tree_shape;
         p.max_value = descs[i].max_value ? descs[i].max_value : MPHF_DEFAULT_MAX_VALUE;
+        p.seeds_per_thread = descs[i].seeds_per_thread;
         outs[i] = nullptr;
         start_job(jobs[i], descs[i].d_keys, descs[i].n, p);
     }
@@ -1750,6 +1685,7 @@ void server_control(mphf_server_t *S) {
             p.leaf_bijection = r->desc.leaf_bijection;
             p.tree_shape = r->desc.tree_shape;
             p.max_value = r->desc.max_value ? r->desc.max_value : MPHF_DEFAULT_MAX_VALUE;
+            p.seeds_per_thread = r->desc.seeds_per_thread;
             start_job(a->job, r->desc.d_keys, r->desc.n, p);
             int rc = a->job.rc ? MPHF_OK : prepare(S, c, *a);
             if (rc != MPHF_OK) fatal(rc);

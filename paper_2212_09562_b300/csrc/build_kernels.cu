@@ -458,9 +458,10 @@ __device__ __forceinline__ ModCTR<MM> make_modct(uint32_t c_from_memory) {
 // smallest working seed wins.
 constexpr int kKeyUnroll = 8;  // key-loop unroll factor of the split search
 
-// SPT seeds per thread and round: two independent hash chains per key load
-// pay off where trials are many (the full nodes of l = 16); one keeps the
-// round (and the work past the winning seed) small elsewhere.
+// SPT seeds per thread and round: independent hash chains per key load (the
+// descriptor's spt: 2 by default where trials are many, the full nodes of
+// l = 16; 1 keeps the round, and the work past the winning seed, small
+// elsewhere; the autotuner may pick another per device).
 template <int SPT, class Cnt, class Mod, class Div>
 __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div,
                                                  const Cnt *lut, Cnt expected, const Mixer &mx,
@@ -1036,15 +1037,20 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             constexpr bool n2 = counter_fits32(L2, field_width(L1), f2);
             using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
             using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
+            // seeds per thread from the descriptor (the autotuner's choice)
             if (m == L1) {
                 const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
-                x = search_lower<(LEAF >= 16 ? 2 : 1), C1>(xs, m, make_modct<L1>(d.red[1]), DivCT<LEAF>(), lut, (C1)expected, mx,
-                                     d.max_value, limit, S);
+                const auto mod = make_modct<L1>(d.red[1]);
+                x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S)
+                  : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S)
+                               : search_lower<1, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S);
                 done = true;
             } else if (m == L2) {
                 const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
-                x = search_lower<(LEAF >= 16 ? 2 : 1), C2>(xs, m, make_modct<L2>(d.red[2]), DivCT<L1>(), lut, (C2)expected, mx,
-                                     d.max_value, limit, S);
+                const auto mod = make_modct<L2>(d.red[2]);
+                x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S)
+                  : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S)
+                               : search_lower<1, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S);
                 done = true;
             }
         }
@@ -1488,7 +1494,12 @@ __device__ __forceinline__ void or_bits(uint64_t *w, uint64_t pos, uint64_t v, u
 __global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                            const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
                            const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
-                           uint32_t bij, uint64_t *gr) {
+                           uint32_t bij, uint64_t *gr, uint64_t cap_bits, uint32_t *status) {
+    // a prepared build reserved cap_bits: a longer code is refused, not written
+    if (bit_pos[nb] > cap_bits) {
+        if (status && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_OVERFLOW);
+        return;
+    }
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -1521,10 +1532,12 @@ __global__ void k_gr_write(const uint64_t *values, const uint16_t *node_m, const
 void launch_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                      const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
                      const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
-                     uint32_t bij, uint64_t *gr, cudaStream_t st) {
+                     uint32_t bij, uint64_t *gr, cudaStream_t st, uint64_t cap_bits,
+                     uint32_t *status) {
     if (nb == 0) return;
     k_gr_write<<<grid_for(nb * 32, 256), 256, 0, st>>>(values, node_m, node_off, bit_pos, nb, tau,
-                                                         fixed_tab, bucket_off, leaf, bij, gr);
+                                                         fixed_tab, bucket_off, leaf, bij, gr,
+                                                         cap_bits, status);
     note_launches(1);
 }
 
@@ -1559,9 +1572,11 @@ __global__ void k_popcount(const uint64_t *words, uint64_t n, uint64_t *out) {
 // Stats: trials up to the stored value, and hash evaluations, per node kind
 // (the smallest stored value is the number of failed trials, Section 5.1).
 __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes,
-                        uint32_t leaf, uint32_t bij, uint32_t tree, unsigned long long *counters) {
+                        const uint64_t *n_nodes_dev, uint32_t leaf, uint32_t bij, uint32_t tree,
+                        unsigned long long *counters) {
     __shared__ unsigned long long acc[8];
     if (threadIdx.x < 8) acc[threadIdx.x] = 0;
+    if (n_nodes_dev && *n_nodes_dev < n_nodes) n_nodes = *n_nodes_dev;  // counted on the device
     __syncthreads();
     const Shape sh = make_shape(leaf, tree);
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n_nodes;
@@ -1581,11 +1596,63 @@ __global__ void k_stats(const uint64_t *values, const uint16_t *node_m, uint64_t
 }
 
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
-                  uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st) {
+                  uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st,
+                  const uint64_t *n_nodes_dev) {
     if (n_nodes == 0) return;
-    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, leaf, bij, tree,
-                                                          (unsigned long long *)counters);
+    k_stats<<<grid_for(n_nodes, 256, 1024), 256, 0, st>>>(values, node_m, n_nodes, n_nodes_dev, leaf, bij,
+                                                          tree, (unsigned long long *)counters);
     note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Elias-Fano for a prepared build, whose code length is known only on the
+// device: the sizes and word offsets of both sequences from the device totals
+// (the same ef_dims as the host), then the writers and the popcounts of the
+// second high-bit vector read them from there.
+__global__ void k_ef_plan(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, EfPlan *p) {
+    if (blockIdx.x || threadIdx.x) return;
+    const EfDims a = ef_dims(nb + 1, cum_keys[nb]), b = ef_dims(nb + 1, bit_pos[nb]);
+    p->L[0] = a.L;
+    p->L[1] = b.L;
+    p->off[0] = 0;                                      // low words of the key offsets
+    p->off[1] = a.low_words;                            // their high words
+    p->off[2] = a.low_words + a.high_words;             // low words of the bit offsets
+    p->off[3] = a.low_words + a.high_words + b.low_words;  // their high words
+    p->high[0] = a.high_words;
+    p->high[1] = b.high_words;
+}
+
+__global__ void k_ef_write_plan(const uint64_t *v, uint64_t k, const EfPlan *p, uint32_t which,
+                                uint64_t *ef) {
+    const uint32_t L = p->L[which];
+    uint64_t *low = ef + p->off[2 * which], *high = ef + p->off[2 * which + 1];
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < k;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x = v[i];
+        if (L) or_bits(low, i * L, x & ((L == 64) ? ~0ull : ((1ull << L) - 1)), L);
+        uint64_t hb = (x >> L) + i;
+        atomicOr((unsigned long long *)&high[hb >> 6], 1ull << (hb & 63));
+    }
+}
+
+// out[w] = ones in word w of the bit offsets' high vector for w < max_words
+// (zero past its end: the buffer is zeroed up to the reserved size), out[max_words] = 0.
+__global__ void k_popcount_plan(const uint64_t *ef, const EfPlan *p, uint64_t max_words, uint64_t *out) {
+    const uint64_t *high = ef + p->off[3];
+    const uint64_t words = p->high[1];
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= max_words;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = i < words ? __popcll(high[i]) : 0;
+}
+
+void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, EfPlan *p,
+                       uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp, cudaStream_t st) {
+    k_ef_plan<<<1, 32, 0, st>>>(cum_keys, bit_pos, nb, p);
+    k_ef_write_plan<<<grid_for(nb + 1, 256), 256, 0, st>>>(cum_keys, nb + 1, p, 0, ef);
+    k_ef_write_plan<<<grid_for(nb + 1, 256), 256, 0, st>>>(bit_pos, nb + 1, p, 1, ef);
+    k_popcount_plan<<<grid_for(max_high1 + 1, 256), 256, 0, st>>>(ef, p, max_high1, rank1);
+    note_launches(4);
+    launch_exclusive_scan(rank1, max_high1 + 1, tmp, st);
 }
 
 // Rank directory of a bit vector: out[w] = ones in words [0, w) (select support).

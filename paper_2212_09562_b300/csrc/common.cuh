@@ -189,4 +189,23 @@ __host__ __device__ __forceinline__ uint32_t counter_width(uint32_t max_part) {
     return w;
 }
 
+// Sizes of an Elias-Fano sequence of k values whose largest is `last`
+// (Section 2.1): L low bits each, high bits in unary.
+struct EfDims {
+    uint32_t L;
+    uint64_t low_words, high_words;
+};
+
+__host__ __device__ inline EfDims ef_dims(uint64_t k, uint64_t last) {
+    EfDims d;
+    d.L = 0;
+    if (last >= k) {
+        uint64_t q = last / k;
+        while (q >>= 1) d.L++;
+    }
+    d.low_words = (k * d.L + 63) / 64;
+    d.high_words = ((last >> d.L) + k + 63) / 64;
+    return d;
+}
+
 }  // namespace rs

@@ -7,7 +7,10 @@ namespace rs {
 
 // Device status bits of one build (host maps them to error codes with the
 // precedence bucket size > duplicate > search cap > wait timeout).
-enum : uint32_t { ST_BUCKET = 1u, ST_DUPLICATE = 2u, ST_LIMIT = 4u, ST_TIMEOUT = 8u, ST_RANGE = 16u };
+enum : uint32_t {
+    ST_BUCKET = 1u, ST_DUPLICATE = 2u, ST_LIMIT = 4u, ST_TIMEOUT = 8u, ST_RANGE = 16u,
+    ST_OVERFLOW = 32u  // a prepared build's packed words outgrew the space reserved for them
+};
 
 // Buckets a build covers: the consecutive range [b_lo, b_lo + nb) of a function
 // whose keys hash to nb_hash buckets (b_lo = 0, nb_hash = nb for a whole function).
@@ -31,6 +34,7 @@ struct InstDesc {
     uint32_t nb;
     uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
     uint32_t leaf_method;        // 0 lock-step, 1 early rejection, 2 early rejection + table
+    uint32_t spt;                // seeds per thread of full lower-level split searches (1, 2, 4)
     const uint8_t *rot_canon;    // per m <= 16 at offset 2^m - 4: canonical rotation of x
     const uint8_t *rot_period;   // same layout: rotation period of x
     const uint32_t *mod_c;       // exact remainder constants per node size (ModRT)
@@ -107,10 +111,13 @@ void launch_serve(const InstDesc *insts, const WorkItem *ring, uint32_t ring_cap
 void launch_gr_lengths(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                        uint64_t nb, const uint8_t *tau, uint32_t leaf, uint32_t bij,
                        uint64_t *bucket_bits, cudaStream_t st);
+// cap_bits / status: a prepared build's reserved code length; a longer code
+// sets ST_OVERFLOW and writes nothing.
 void launch_gr_write(const uint64_t *values, const uint16_t *node_m, const uint64_t *node_off,
                      const uint64_t *bit_pos, uint64_t nb, const uint8_t *tau,
                      const uint32_t *fixed_tab, const uint64_t *bucket_off, uint32_t leaf,
-                     uint32_t bij, uint64_t *gr, cudaStream_t st);
+                     uint32_t bij, uint64_t *gr, cudaStream_t st, uint64_t cap_bits = ~0ull,
+                     uint32_t *status = nullptr);
 void launch_ef_write(const uint64_t *v, uint64_t k, uint32_t L, uint64_t *low, uint64_t *high,
                      cudaStream_t st);
 // dir[w] = ones in words [0, w), w in [0, nwords]; tmp: scan_tmp_words(nwords + 1).
@@ -118,8 +125,22 @@ void launch_rank_dir(const uint64_t *words, uint64_t nwords, uint64_t *dir, uint
                      cudaStream_t st);
 // sel[j] = the word holding one number 64 j (0-based), from the rank directory.
 void launch_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel, cudaStream_t st);
+// n_nodes bounds the grid; n_nodes_dev (if given) is the count on the device.
 void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nodes, uint32_t leaf,
-                  uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st);
+                  uint32_t bij, uint32_t tree, uint64_t *counters, cudaStream_t st,
+                  const uint64_t *n_nodes_dev = nullptr);
+// Elias-Fano of a prepared build (code length known only on the device): the
+// sizes and word offsets of both sequences, as ef_dims gives them.
+struct EfPlan {
+    uint32_t L[2];
+    uint64_t off[4];   // low and high words of the key offsets, then of the bit offsets
+    uint64_t high[2];  // high words of each sequence
+};
+// Writes both sequences into the zeroed ef (sized for the largest possible
+// code), and rank1 = the rank directory of the bit offsets' high vector over
+// max_high1 words (tmp: scan_tmp_words(max_high1 + 1)).
+void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, EfPlan *p,
+                       uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp, cudaStream_t st);
 
 // Building one function on several GPUs (bucket ranges, Section 5.2).
 // Keys grouped by the rank owning their bucket (nb buckets, `world` ranges):

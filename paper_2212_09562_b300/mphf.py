@@ -27,6 +27,7 @@ EBUSY = -6
 EBUCKET = -7
 ENOTIMPL = -8
 ETIMEOUT = -9
+ECAPACITY = -10
 MAX_BUCKET = 4096
 VERIFY_STATIC_MAX_KEYS = 1 << 20
 DEFAULT_MAX_VALUE = (1 << 40) - 1
@@ -97,7 +98,8 @@ class BuildParams(ctypes.Structure):
                 ("key_bytes", ctypes.c_uint32), ("leaf_bijection", ctypes.c_uint32),
                 ("max_value", ctypes.c_uint64), ("allocator", ctypes.c_void_p),
                 ("threads_per_block", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
-                ("leaf_method", ctypes.c_uint32), ("tree_shape", ctypes.c_uint32)]
+                ("leaf_method", ctypes.c_uint32), ("tree_shape", ctypes.c_uint32),
+                ("seeds_per_thread", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Info(ctypes.Structure):
@@ -131,7 +133,7 @@ class BuildDesc(ctypes.Structure):
     _fields_ = [("d_keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("leaf_size", ctypes.c_uint32),
                 ("bucket_size", ctypes.c_uint32), ("key_bytes", ctypes.c_uint32),
                 ("leaf_bijection", ctypes.c_uint32), ("max_value", ctypes.c_uint64),
-                ("tree_shape", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("tree_shape", ctypes.c_uint32), ("seeds_per_thread", ctypes.c_uint32)]
 
 
 # Every entry point of include/mphf.h: name -> (restype, argtypes)
@@ -160,6 +162,9 @@ SIGNATURES = {
     "mphf_server_submit": (_I, [_P, _P, _P]),
     "mphf_server_poll": (_I, [_P, _U64, _U32, _P, _P, _P]),
     "mphf_server_destroy": (_I, [_P]),
+    "mphf_build_prepare": (_I, [_U64, _P, _U64, _P]),
+    "mphf_build_enqueue": (_I, [_P, _P, _P]),
+    "mphf_build_finish": (_I, [_P, _P]),
     "mphf_shard_route": (_I, [_P, _U64, _U32, _U64, _U32, _U32, _P, _P, _P]),
     "mphf_build_shard": (_I, [_P, _U64, _U64, _P, _U32, _U32, _P, _P]),
     "mphf_shard_pack": (_I, [_P, _P, _P, _P]),
@@ -266,22 +271,24 @@ class MPHF:
               max_value: int = DEFAULT_MAX_VALUE, threads_per_block: int = 0,
               blocks_per_sm: int = 0, stream=None, tuned: bool = False,
               leaf_method: int | None = None, tree: int = TREE_RECSPLIT,
-              allocator: "TorchAllocator | None" = None) -> "MPHF":
+              allocator: "TorchAllocator | None" = None, seeds_per_thread: int = 0) -> "MPHF":
         """rotation: True/False or PLAIN, ROTATION, SHOCKHASH (the leaf method);
         tree: TREE_RECSPLIT or TREE_FANOUT2;
-        tuned=True takes the launch shape from the autotuner's cache;
+        tuned=True takes the launch shape and seeds per thread from the
+        autotuner's cache (the library default where nothing is cached);
         leaf_method: LEAF_LOCKSTEP (default), LEAF_EARLY or LEAF_TABLE;
         allocator: device memory hooks (default: the library's cudaMallocAsync)."""
         n, kb = key_layout(keys)
-        if tuned and not threads_per_block and not blocks_per_sm:
+        if tuned and not threads_per_block and not blocks_per_sm and not seeds_per_thread:
             from .autotune import tuned as cached_shape
-            threads_per_block, blocks_per_sm = cached_shape(leaf_size, rotation, tree)
+            threads_per_block, blocks_per_sm, seeds_per_thread = cached_shape(leaf_size, rotation, tree)
         p = default_params()
         p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, kb
         p.leaf_bijection = bijection(rotation)
         p.tree_shape = tree
         p.max_value = max_value
         p.threads_per_block, p.blocks_per_sm = threads_per_block, blocks_per_sm
+        p.seeds_per_thread = seeds_per_thread
         if leaf_method is not None:
             p.leaf_method = leaf_method
         if allocator is not None:
@@ -291,6 +298,38 @@ class MPHF:
                                  _stream(stream), ctypes.byref(h))
         _check(rc, "mphf_build_ex")
         return cls(h.value, allocator)
+
+    @classmethod
+    def prepare(cls, n: int, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
+                key_bytes: int = 8, tree: int = TREE_RECSPLIT, max_value: int = DEFAULT_MAX_VALUE,
+                seeds_per_thread: int = 0, gr_capacity_bits: int = 0) -> "MPHF":
+        """A build of exactly n keys whose device work can be captured in a CUDA
+        graph: enqueue(keys) issues it, finish() makes the function usable."""
+        _torch()
+        p = default_params()
+        p.leaf_size, p.bucket_size, p.key_bytes = leaf_size, bucket_size, key_bytes
+        p.leaf_bijection, p.tree_shape = bijection(rotation), tree
+        p.max_value, p.seeds_per_thread = max_value, seeds_per_thread
+        h = ctypes.c_void_p()
+        _check(lib().mphf_build_prepare(n, ctypes.byref(p), gr_capacity_bits, ctypes.byref(h)),
+               "mphf_build_prepare")
+        obj = cls.__new__(cls)
+        obj._h, obj._allocator, obj.info = h, None, Info()
+        _check(lib().mphf_get_info(h, ctypes.byref(obj.info)), "mphf_get_info")
+        return obj
+
+    def enqueue(self, keys, stream=None):
+        """Issues the prepared build of `keys` (n keys, the prepared key size) on
+        the stream; capturable."""
+        n, kb = key_layout(keys)
+        if n != self.info.n or kb != self.info.key_bytes:
+            raise ValueError("keys must be the prepared number and size")
+        _check(lib().mphf_build_enqueue(self._h, keys.data_ptr(), _stream(stream)), "mphf_build_enqueue")
+
+    def finish(self, stream=None):
+        """Waits for the enqueued build and makes the function usable (raises its error)."""
+        _check(lib().mphf_build_finish(self._h, _stream(stream)), "mphf_build_finish")
+        _check(lib().mphf_get_info(self._h, ctypes.byref(self.info)), "mphf_get_info")
 
     @classmethod
     def build_host(cls, keys: np.ndarray, leaf_size: int = 16, bucket_size: int = 2000,
@@ -435,16 +474,23 @@ def tau_table(leaf_size: int, rotation, max_m: int = MAX_BUCKET,
 
 
 def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation=True,
-                max_value: int = 0, stream=None, tree: int = TREE_RECSPLIT) -> list[MPHF]:
-    """Many independent builds in one call (see mphf_build_batch)."""
+                max_value: int = 0, stream=None, tree: int = TREE_RECSPLIT,
+                tuned: bool = True) -> list[MPHF]:
+    """Many independent builds in one call (see mphf_build_batch).  tuned:
+    each build's seeds per thread from the autotuner's cache for its leaf size
+    (the library default where nothing is cached)."""
     count = len(keys_list)
     if len(leaf_sizes) != count:
         raise ValueError("one leaf size per key set")
+    spt = {}
+    if tuned:
+        from .autotune import tuned as cached_shape
+        spt = {l: cached_shape(l, rotation, tree)[2] for l in set(leaf_sizes)}
     descs = (BuildDesc * max(count, 1))()
     for i, (k, l) in enumerate(zip(keys_list, leaf_sizes)):
         n, kb = key_layout(k)
         descs[i] = BuildDesc(k.data_ptr() if n else None, n, l, bucket_size, kb,
-                             bijection(rotation), max_value, tree, 0)
+                             bijection(rotation), max_value, tree, spt.get(l, 0))
     outs = (ctypes.c_void_p * max(count, 1))()
     sts = (ctypes.c_int * max(count, 1))()
     rc = lib().mphf_build_batch(descs, count, _stream(stream), outs, sts)
@@ -470,10 +516,10 @@ class Server:
         self._keep = {}  # ticket -> key tensor, alive until the request is polled
 
     def submit(self, keys, leaf_size: int = 16, bucket_size: int = 2000, rotation=True,
-               max_value: int = 0, tree: int = TREE_RECSPLIT) -> int:
+               max_value: int = 0, tree: int = TREE_RECSPLIT, seeds_per_thread: int = 0) -> int:
         n, kb = key_layout(keys)
         d = BuildDesc(keys.data_ptr() if n else None, n, leaf_size, bucket_size, kb,
-                      bijection(rotation), max_value, tree, 0)
+                      bijection(rotation), max_value, tree, seeds_per_thread)
         t = ctypes.c_uint64()
         _check(lib().mphf_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)),
                "mphf_server_submit")

@@ -17,12 +17,12 @@ def test_cache_keys_and_lookups(tmp_path, monkeypatch):
             A._key(16, True, M.TREE_FANOUT2)}
     assert len(keys) == 5
     assert A._key(16, True) == "B300|l=16|rot=1"  # the RecSplit tree keeps the plain key
-    data = {A._key(16, True): {"threads": 512, "blocks_per_sm": 2},
+    data = {A._key(16, True): {"threads": 512, "blocks_per_sm": 2, "seeds_per_thread": 4},
             A._key(24, M.SHOCKHASH, M.TREE_FANOUT2): {"threads": 256, "blocks_per_sm": 0}}
     (tmp_path / "tune.json").write_text(json.dumps(data))
-    assert A.tuned(16, True) == (512, 2)
+    assert A.tuned(16, True) == (512, 2, 4)
     assert A.tuned(16, True, M.TREE_FANOUT2) == A.DEFAULT
-    assert A.tuned(24, M.SHOCKHASH, M.TREE_FANOUT2) == (256, 0)
+    assert A.tuned(24, M.SHOCKHASH, M.TREE_FANOUT2) == (256, 0, 0)  # an entry without the field
     assert A.tuned(24, M.SHOCKHASH) == A.DEFAULT
     monkeypatch.setattr(A, "_device_name", lambda: "another GPU")
     assert A.tuned(16, True) == A.DEFAULT
