@@ -589,6 +589,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
     uint32_t *head = nullptr;
     InstDesc *d_inst = nullptr;
     WorkItem *items = nullptr;
+    StealQueue *steal = nullptr;
     std::vector<InstDesc> hinst;
     std::vector<uint32_t> inst_job;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -622,9 +623,11 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
         launch_exclusive_scan(c.size_hist, 4098, c.scan_tmp, st);
         d_inst = (InstDesc *)c.mem.get(hinst.size() * sizeof(InstDesc));
         items = (WorkItem *)c.mem.get(total_slots * sizeof(WorkItem));
-        if (!d_inst || !items) {
+        steal = (StealQueue *)c.mem.get(kStealBytes);
+        if (!d_inst || !items || !steal) {
             grc = MPHF_ENOMEM;
         } else if (cudaMemsetAsync(items, 0xFF, total_slots * sizeof(WorkItem), st) != cudaSuccess ||
+                   cudaMemsetAsync(steal, 0, kStealBytes, st) != cudaSuccess ||
                    cudaMemcpyAsync(d_inst, hinst.data(), hinst.size() * sizeof(InstDesc),
                                    cudaMemcpyHostToDevice, st) != cudaSuccess) {
             grc = MPHF_ECUDA;
@@ -637,7 +640,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
             if (!threads) threads = default_threads(jp);
             SearchLaunch L = plan_search_launch(max_m, (uint32_t)total_slots, threads, blocks_per_sm);
             cudaEventRecord(ev[2], st);
-            launch_search(d_inst, items, (uint32_t)total_slots, head, L, st);
+            launch_search(d_inst, (uint32_t)hinst.size(), items, (uint32_t)total_slots, head, L, steal, st);
             if (cudaGetLastError() != cudaSuccess) grc = MPHF_ECUDA;
         }
     } else {
@@ -668,6 +671,7 @@ int run_jobs(std::vector<Job> &jobs, cudaStream_t st, const mphf_allocator *shar
     c.mem.put(head);
     c.mem.put(d_inst);
     c.mem.put(items);
+    c.mem.put(steal);
     c.release();
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);

@@ -353,6 +353,7 @@ struct BlockState {
     int sp;
     uint32_t nleaves, leaf_next, flags, item;
     unsigned long long found, claim;
+    int give;  // stack entries to give away now
     uint32_t cnt[16];
     unsigned long long lut64[16];  // child -> counter increment (last child: 0)
     uint32_t lut32[16];
@@ -1196,54 +1197,192 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
     }
 }
 
-// One bucket's whole splitting tree (Section 2.2): the inner nodes depth
-// first, then every leaf's bijection search, values written in preorder.
+// Giving subtrees away (the tail of a search).  Buckets take random times
+// (geometric trial counts), so when the bucket queue runs dry the blocks
+// finish one by one and idle while the last ones work.  From then on a block
+// whose stack holds two or more inner nodes not yet started, while some
+// block is idle, gives all but the next one away: it writes their keys back
+// to the build's grouped-key array and publishes (build, bucket, key offset,
+// size, depth, preorder index) in the steal queue; an idle block takes one,
+// loads its keys and processes it like a bucket.  Every node is still
+// searched by one block with the same keys and salt, so the stored values
+// do not change.  A published node is never lost: a block leaves only when
+// the queue is empty and no block is busy, and a block that published nodes
+// takes from the queue itself after its own work.
+struct StealCtx {
+    StealQueue *q;           // nullptr: no stealing (the serving search)
+    const uint32_t *bucket_head;
+    uint32_t nitems, cap;
+};
+constexpr uint32_t kStealReady = 1u << 31;
+
+// Thread 0: the number of bottom stack entries to give away now.
+__device__ __forceinline__ int donation(const StealCtx &X, const BlockState &S) {
+    if (!X.q || S.sp < 2) return 0;
+    if (atomicAdd(&X.q->idle, 0u) == 0) return 0;
+    if (atomicAdd((unsigned int *)X.bucket_head, 0u) < X.nitems) return 0;  // buckets still queued
+    return S.sp - 1;
+}
+
 template <int LEAF>
-__device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
-                               BlockState &S) {
+__device__ __forceinline__ void give_away(const InstDesc &d, uint32_t inst, uint32_t bucket, uint64_t kbeg,
+                                          uint32_t goff, const SmemArrays &A, BlockState &S,
+                                          const StealCtx &X) {
+    const uint32_t tid = threadIdx.x, T = blockDim.x;
+    const int give = S.give;
+    uint64_t *glo = (uint64_t *)d.lo;  // the build's grouped-key scratch
+    uint8_t *gbb = (uint8_t *)d.bb;
+    for (int e = 0; e < give; e++) {
+        const uint32_t off = S.st_off[e], m = S.st_m[e];
+        for (uint32_t i = tid; i < m; i += T) {
+            glo[kbeg + goff + off + i] = A.lo[off + i];
+            gbb[kbeg + goff + off + i] = A.bb[off + i];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        int kept = 0;
+        for (int e = 0; e < give; e++) {
+            const uint32_t slot = atomicAdd(&X.q->tail, 1u);
+            if (slot >= X.cap) {  // queue full: keep the node
+                S.st_off[kept] = S.st_off[e];
+                S.st_m[kept] = S.st_m[e];
+                S.st_depth[kept] = S.st_depth[e];
+                S.st_pidx[kept] = S.st_pidx[e];
+                kept++;
+                continue;
+            }
+            unsigned int *w = X.q->items[slot].w;
+            __stcg(w + 0, inst);
+            __stcg(w + 1, bucket);
+            __stcg(w + 2, (goff + S.st_off[e]) | ((uint32_t)S.st_m[e] << 16));
+            __threadfence();
+            atomicExch(w + 3, (uint32_t)S.st_pidx[e] | ((uint32_t)S.st_depth[e] << 16) | kStealReady);
+        }
+        const int top = S.sp - 1;  // the node this block takes next stays
+        S.st_off[kept] = S.st_off[top];
+        S.st_m[kept] = S.st_m[top];
+        S.st_depth[kept] = S.st_depth[top];
+        S.st_pidx[kept] = S.st_pidx[top];
+        S.sp = kept + 1;
+    }
+    __syncthreads();
+}
+
+// One unit of search work (Section 2.2): the subtree of m0 keys at key offset
+// goff of a bucket (a whole bucket: goff = 0, m0 = its size), its inner nodes
+// depth first, then every leaf's bijection search, values written in preorder.
+template <int LEAF>
+__device__ __forceinline__ void process_item(const InstDesc &d, uint32_t inst, uint32_t bucket, uint32_t goff,
+                                             uint32_t m0, uint32_t depth0, uint32_t pidx0,
+                                             const SmemArrays &A, BlockState &S, const StealCtx &X) {
     const uint32_t tid = threadIdx.x, T = blockDim.x;
     const Shape sh = make_shape(LEAF ? (uint32_t)LEAF : d.leaf, d.tree);
     // a build's arrays are read past L1 (ld.global.cg): a serving search runs
-    // across requests whose arrays may reuse the addresses of earlier ones
+    // across requests whose arrays may reuse the addresses of earlier ones,
+    // and keys given away were written by another block of this launch
     const uint64_t kbeg = __ldcg(d.bucket_off + bucket);
-    const uint64_t M = __ldcg(d.bucket_off + bucket + 1) - kbeg;
     const uint64_t nbase = __ldcg(d.node_off + bucket);
-    if (M <= 1 || M > 4096) return;  // nothing stored / refused by the plan
-    for (uint32_t i = tid; i < M; i += T) {
-        A.lo[i] = __ldcg(d.lo + kbeg + i);
-        A.bb[i] = __ldcg(d.bb + kbeg + i);
+    if (m0 <= 1 || m0 > 4096) return;  // nothing stored / refused by the plan
+    for (uint32_t i = tid; i < m0; i += T) {
+        A.lo[i] = __ldcg(d.lo + kbeg + goff + i);
+        A.bb[i] = __ldcg(d.bb + kbeg + goff + i);
     }
     if (tid == 0) {
         S.sp = 0;
         S.nleaves = 0;
         S.leaf_next = 0;
         S.flags = 0;
-        if (M <= sh.leaf) {
+        if (m0 <= sh.leaf) {
             A.leaf_off[0] = 0;
-            A.leaf_m[0] = (uint8_t)M;
-            A.leaf_pidx[0] = 0;
+            A.leaf_m[0] = (uint8_t)m0;
+            A.leaf_pidx[0] = (uint16_t)pidx0;
             S.nleaves = 1;
         } else {
             S.st_off[0] = 0;
-            S.st_m[0] = (uint16_t)M;
-            S.st_depth[0] = 0;
-            S.st_pidx[0] = 0;
+            S.st_m[0] = (uint16_t)m0;
+            S.st_depth[0] = (uint8_t)depth0;
+            S.st_pidx[0] = (uint16_t)pidx0;
             S.sp = 1;
         }
     }
     __syncthreads();
     for (;;) {
         if (S.sp == 0 || S.flags) break;
+        if (tid == 0) S.give = donation(X, S);
+        __syncthreads();
+        if (S.give) give_away<LEAF>(d, inst, bucket, kbeg, goff, A, S, X);
         const int k = S.sp - 1;
         const uint32_t off = S.st_off[k], m = S.st_m[k], depth = S.st_depth[k], pidx = S.st_pidx[k];
         __syncthreads();
         if (tid == 0) S.sp = k;
-        split_node<LEAF>(d, sh, off, m, depth, pidx, nbase, (uint32_t)M, A, S);
+        split_node<LEAF>(d, sh, off, m, depth, pidx, nbase, m0, A, S);
     }
     if (!S.flags) leaf_phase<LEAF>(d, nbase, A, S);
     __syncthreads();
     if (tid == 0 && S.flags) atomicOr(d.status, S.flags);
     __syncthreads();
+}
+
+template <int LEAF>
+__device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucket, const SmemArrays &A,
+                                               BlockState &S) {
+    const uint32_t m = (uint32_t)(__ldcg(d.bucket_off + bucket + 1) - __ldcg(d.bucket_off + bucket));
+    process_item<LEAF>(d, 0, bucket, 0, m > 4096 ? 4097u : m, 0, 0, A, S, StealCtx{nullptr, nullptr, 0, 0});
+}
+
+// Thread 0 of an idle block: a node from the steal queue, or ~0u when the
+// queue is empty and no block is busy (nothing more can be given away).
+// Waits are bounded: leaving is always safe, since a block that gave nodes
+// away takes from the queue after its own work.
+__device__ uint32_t steal_claim(const StealCtx &X, const InstDesc *insts, uint32_t ninst) {
+    StealQueue *Q = X.q;
+    atomicAdd(&Q->idle, 1u);
+    uint32_t got = ~0u;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (uint32_t spin = 0; spin < (1u << 24); spin++) {
+        const uint32_t h = atomicAdd(&Q->head, 0u);
+        uint32_t t = atomicAdd(&Q->tail, 0u);
+        t = t < X.cap ? t : X.cap;
+        if (h < t) {
+            if (atomicCAS(&Q->head, h, h + 1) == h) {
+                got = h;
+                break;
+            }
+            continue;
+        }
+        if (atomicAdd(&Q->busy, 0u) == 0) {
+            __threadfence();
+            t = atomicAdd(&Q->tail, 0u);
+            t = t < X.cap ? t : X.cap;
+            if (atomicAdd(&Q->head, 0u) >= t) break;
+            continue;
+        }
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if (now - t0 > 30000000000ull) break;  // 30 s
+        __nanosleep(2000);
+    }
+    if (got != ~0u) {
+        atomicAdd(&Q->busy, 1u);
+        // the publisher's last store may still be on its way (bounded wait)
+        bool ready = false;
+        for (uint32_t spin = 0; spin < (1u << 22) && !ready; spin++) {
+            ready = (atomicAdd(&Q->items[got].w[3], 0u) & kStealReady) != 0;
+            if (!ready) __nanosleep(100);
+        }
+        if (!ready) {  // cannot happen unless the device misbehaves: fail every build of the launch
+            for (uint32_t i = 0; i < ninst; i++)
+                if (insts[i].status) atomicOr(insts[i].status, ST_TIMEOUT);
+            atomicSub(&Q->busy, 1u);
+            got = ~0u;
+        }
+        __threadfence();
+    }
+    atomicSub(&Q->idle, 1u);
+    return got;
 }
 
 // Dynamic shared memory of the search kernel for buckets of at most `cap`
@@ -1262,8 +1401,9 @@ struct SmemLayout {
 // The persistent search (the brute-force searches of Section 2.2 in the
 // parallel form of Section 5.3): blocks take buckets from a device queue,
 // largest first, and run process_bucket on each.
-__global__ void __launch_bounds__(512) k_search(const InstDesc *insts, const WorkItem *items,
-                                                uint32_t nitems, uint32_t *head, uint32_t cap) {
+__global__ void __launch_bounds__(512) k_search(const InstDesc *insts, uint32_t ninst, const WorkItem *items,
+                                                uint32_t nitems, uint32_t *head, uint32_t cap,
+                                                StealQueue *steal, uint32_t steal_cap) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ BlockState S;
     const SmemLayout lay(cap);
@@ -1275,21 +1415,50 @@ __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, const Wor
     A.leaf_off = (uint16_t *)(dyn + 18u * lay.P);
     A.leaf_pidx = A.leaf_off + lay.nl;
     A.leaf_m = (uint8_t *)(A.leaf_pidx + lay.nl);
+    const StealCtx X{steal, head, nitems, steal_cap};
     for (;;) {
-        if (threadIdx.x == 0) S.item = atomicAdd(head, 1u);
+        if (threadIdx.x == 0) {
+            S.item = atomicAdd(head, 1u);
+            if (S.item < nitems && steal) atomicAdd(&steal->busy, 1u);
+            const uint32_t g = S.item < nitems || !steal ? ~0u : steal_claim(X, insts, ninst);
+            S.claim = g < steal_cap ? (unsigned long long)g : ~0ull;  // ~0: nothing was claimed
+        }
         __syncthreads();
         const uint32_t it = S.item;
+        const unsigned long long got = S.claim;
         __syncthreads();
-        if (it >= nitems) break;
-        const WorkItem w = items[it];
-        if (w.inst == 0xFFFFFFFFu) continue;  // empty slot (its build failed its plan)
-        const InstDesc d = insts[w.inst];
-        switch (d.leaf) {
-            case 8: process_bucket<8>(d, w.bucket, A, S); break;
-            case 12: process_bucket<12>(d, w.bucket, A, S); break;
-            case 16: process_bucket<16>(d, w.bucket, A, S); break;
-            default: process_bucket<0>(d, w.bucket, A, S); break;
+        uint32_t inst, bucket, goff = 0, m0 = 0, depth = 0, pidx = 0;
+        if (it < nitems) {  // a whole bucket
+            const WorkItem w = items[it];
+            inst = w.inst;
+            bucket = w.bucket;
+            if (inst != 0xFFFFFFFFu) {  // else an empty slot (its build failed its plan)
+                const InstDesc &dd = insts[inst];
+                const uint64_t mm = __ldcg(dd.bucket_off + bucket + 1) - __ldcg(dd.bucket_off + bucket);
+                m0 = mm > 4096 ? 4097u : (uint32_t)mm;
+            }
+        } else if (got != ~0ull) {  // a subtree another block gave away
+            const unsigned int *w = steal->items[got].w;
+            inst = __ldcg(w + 0);
+            bucket = __ldcg(w + 1);
+            const uint32_t w2 = __ldcg(w + 2), w3 = __ldcg(w + 3);
+            goff = w2 & 0xFFFFu;
+            m0 = w2 >> 16;
+            pidx = w3 & 0xFFFFu;
+            depth = (w3 >> 16) & 0xFFu;
+        } else {
+            break;
         }
+        if (inst != 0xFFFFFFFFu) {
+            const InstDesc d = insts[inst];
+            switch (d.leaf) {
+                case 8: process_item<8>(d, inst, bucket, goff, m0, depth, pidx, A, S, X); break;
+                case 12: process_item<12>(d, inst, bucket, goff, m0, depth, pidx, A, S, X); break;
+                case 16: process_item<16>(d, inst, bucket, goff, m0, depth, pidx, A, S, X); break;
+                default: process_item<0>(d, inst, bucket, goff, m0, depth, pidx, A, S, X); break;
+            }
+        }
+        if (threadIdx.x == 0 && steal) atomicSub(&steal->busy, 1u);
     }
 }
 
@@ -1426,10 +1595,11 @@ SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads
     return L;
 }
 
-void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
-                   const SearchLaunch &L, cudaStream_t st) {
+void launch_search(const InstDesc *d_inst, uint32_t ninst, const WorkItem *d_items, uint32_t items,
+                   uint32_t *d_head, const SearchLaunch &L, StealQueue *steal, cudaStream_t st) {
     if (items == 0) return;
-    k_search<<<L.blocks, L.threads, L.smem_bytes, st>>>(d_inst, d_items, items, d_head, L.cap);
+    k_search<<<L.blocks, L.threads, L.smem_bytes, st>>>(d_inst, ninst, d_items, items, d_head, L.cap,
+                                                        steal, kStealCap);
     note_launches(1);
 }
 

@@ -99,8 +99,20 @@ void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
                     const BucketRange &R, const uint64_t *bucket_off, uint32_t *cursor, uint64_t *lo,
                     uint8_t *bb, uint32_t *status, cudaStream_t st);
 SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads, uint32_t blocks_per_sm);
-void launch_search(const InstDesc *d_inst, const WorkItem *d_items, uint32_t items, uint32_t *d_head,
-                   const SearchLaunch &L, cudaStream_t st);
+// Nodes given away by busy blocks to idle ones at the end of a search (see
+// k_search): a node is (build, bucket, key offset | size << 16, preorder
+// index | depth << 16 | ready bit); zero it (kStealBytes) before each launch.
+struct StealItem {
+    unsigned int w[4];
+};
+struct StealQueue {
+    unsigned int tail, head, idle, busy;
+    StealItem items[1];  // kStealCap entries
+};
+constexpr uint32_t kStealCap = 32768;
+constexpr size_t kStealBytes = 16 + sizeof(StealItem) * kStealCap;
+void launch_search(const InstDesc *d_inst, uint32_t ninst, const WorkItem *d_items, uint32_t items,
+                   uint32_t *d_head, const SearchLaunch &L, StealQueue *steal, cudaStream_t st);
 // The serving search (reads work from a ring the host appends to; see k_serve).
 ServeLaunch plan_serve_launch(uint32_t threads, uint32_t reserved_sms);
 void launch_serve(const InstDesc *insts, const WorkItem *ring, uint32_t ring_cap, ServeCtl *ctl,

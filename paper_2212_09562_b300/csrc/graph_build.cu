@@ -36,6 +36,7 @@ struct BuildPlan {
     WorkItem *items = nullptr;
     InstDesc *d_inst = nullptr;
     EfPlan *efp = nullptr;
+    StealQueue *steal = nullptr;
     uint64_t *host = nullptr;  // pinned: status word, node total, bit total, 8 counters
 };
 
@@ -43,7 +44,8 @@ void release_plan(mphf_t *h, Mem &mem) {
     BuildPlan *b = h ? h->plan : nullptr;
     if (!b) return;
     void *ptrs[] = {b->lo_s, b->counters, b->scan_tmp, b->size_hist, b->bb_s, b->cursor, b->small,
-                    b->blk, b->size_cursor, b->head, b->node_m, b->items, b->d_inst, b->efp};
+                    b->blk, b->size_cursor, b->head, b->node_m, b->items, b->d_inst, b->efp,
+                    b->steal};
     for (void *p : ptrs) mem.put(p);
     if (b->host) cudaFreeHost(b->host);
     delete b;
@@ -136,10 +138,11 @@ int mphf_build_prepare(uint64_t n, const mphf_build_params *p, uint64_t gr_capac
     b->items = (WorkItem *)mem.get(nb * sizeof(WorkItem));
     b->d_inst = (InstDesc *)mem.get(sizeof(InstDesc));
     b->efp = (EfPlan *)mem.get(sizeof(EfPlan));
+    b->steal = (StealQueue *)mem.get(kStealBytes);
     if (b->sort_g) b->blk = (uint32_t *)mem.get((uint64_t)b->sort_g * nb * 4);
     bool ok = h->cum_keys && h->node_off && h->bit_pos && h->values && h->gr && h->ef && h->ef_dir &&
               b->lo_s && b->bb_s && b->node_m && b->cursor && b->small && b->counters && b->scan_tmp &&
-              b->size_hist && b->size_cursor && b->head && b->items && b->d_inst && b->efp &&
+              b->size_hist && b->size_cursor && b->head && b->items && b->d_inst && b->efp && b->steal &&
               (!b->sort_g || b->blk);
     if (!ok) {
         cudaStreamSynchronize(0);
@@ -222,6 +225,7 @@ int mphf_build_enqueue(mphf_t *h, const void *d_keys, void *stream) {
                  {b.size_hist, 4098 * 8},
                  {b.size_cursor, 4097 * 4},
                  {b.head, 64},
+                 {b.steal, kStealBytes},
                  {h->gr, (b.cap_bits / 64 + 2) * 8},
                  {h->ef, (e0.low_words + e0.high_words + b.max_low1 + b.max_high1 + 1) * 8},
                  {h->ef_dir, (h->ef_dir_len[0] + h->ef_dir_len[1] + 2 * h->ef_sel_len) * 8}};
@@ -245,7 +249,7 @@ int mphf_build_enqueue(mphf_t *h, const void *d_keys, void *stream) {
         launch_scatter(d_keys, n, kb, nb, R, h->cum_keys, b.cursor, b.lo_s, b.bb_s, b.small, st);
     launch_exclusive_scan(b.size_hist, 4098, b.scan_tmp, st);
     launch_items_by_size(h->cum_keys, nb, b.size_hist, b.size_cursor, b.items, 0, st);
-    launch_search(b.d_inst, b.items, (uint32_t)nb, b.head, b.L, st);
+    launch_search(b.d_inst, 1, b.items, (uint32_t)nb, b.head, b.L, b.steal, st);
     // a8: Golomb-Rice lengths and bits, Elias-Fano from the device totals
     launch_gr_lengths(h->values, b.node_m, h->node_off, nb, h->tabs.tau, leaf, bij, h->bit_pos, st);
     launch_exclusive_scan(h->bit_pos, k, b.scan_tmp, st);
