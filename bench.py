@@ -48,10 +48,11 @@ IMAD_FORMS_PER_EVAL = {"mad.wide.u32": 3, "mad.lo.u32": 5, "mad.hi.u32": 1}
 # (3 each), exact remainder (3 multiply forms + 3 shift/add/carry), counter (3).
 OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # DRAM bytes the search kernel moves per key (lo word and rotation bit read
-# once per bucket), from dram__bytes_read.sum + dram__bytes_write.sum of one
-# ncu capture of k_search on 600,000 keys of rot_l16: 6,386,432 B.  The
+# once per bucket, plus the keys of nodes given to other blocks), from
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_search
+# on 3,000,000 keys of rot_l16 (a multi-wave launch): 28,126,208 B.  The
 # traffic of a launch grows with its key count.
-SEARCH_DRAM_BYTES_PER_KEY = 6_386_432 / 600_000
+SEARCH_DRAM_BYTES_PER_KEY = 28_126_208 / 3_000_000
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 
 
@@ -95,7 +96,7 @@ def search_roofline(peaks: dict, evals_per_launch: float, launch_ms: float, benc
                       "frac": evals_per_s * OPS_PER_EVAL / issue},
             "evals_per_launch": evals_per_launch, "launch_ms": launch_ms,
             "traffic": traffic,
-            "traffic_basis": "ncu DRAM bytes of k_search at 6e5 keys of rot_l16, scaled by n"}
+            "traffic_basis": "ncu DRAM bytes of k_search at 3e6 keys of rot_l16, scaled by n"}
 
 
 def parse():
@@ -111,6 +112,8 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="override the key count (profiling runs)")
     ap.add_argument("--mode", choices=["build", "serve", "batch", "peaks"], default="build")
     ap.add_argument("--requests", type=int, default=24, help="serve mode: requests per run")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="build with the library's default search shape (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the serve leg in the default run (0 = skip)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve mode: Poisson arrivals per second")
@@ -475,15 +478,15 @@ def run_ours(args):
     # launch shape and seeds per thread from the autotuner (tuned now if this
     # device has no cached choice for the workload's leaf size)
     from paper_2212_09562_b300 import autotune as A
-    if A.tuned(w.leaf, w.rotation, w.tree) == A.DEFAULT:
+    if not args.no_tune and A.tuned(w.leaf, w.rotation, w.tree) == A.DEFAULT:
         A.tune(w.leaf, w.rotation, bucket=w.bucket, tree=w.tree)
-    shape = A.tuned(w.leaf, w.rotation, w.tree)
+    shape = A.DEFAULT if args.no_tune else A.tuned(w.leaf, w.rotation, w.tree)
 
     def one_build(k):
         """(function, the part this rank searched): the whole build on one GPU,
         else one function over all ranks' keys in bucket-range shards."""
         if world == 1:
-            g = M.MPHF.build(k, w.leaf, w.bucket, w.rotation, tree=w.tree, tuned=True)
+            g = M.MPHF.build(k, w.leaf, w.bucket, w.rotation, tree=w.tree, tuned=not args.no_tune)
             return g, g
         return S.build_sharded(k, w.leaf, w.bucket, w.rotation, tree=w.tree)
 
