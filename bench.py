@@ -479,7 +479,8 @@ def run_ours(args):
     # device has no cached choice for the workload's leaf size)
     from paper_2212_09562_b300 import autotune as A
     if not args.no_tune and A.tuned(w.leaf, w.rotation, w.tree) == A.DEFAULT:
-        A.tune(w.leaf, w.rotation, bucket=w.bucket, tree=w.tree)
+        # tuned on the workload's own size up to 3e6 keys (the best shape depends on it)
+        A.tune(w.leaf, w.rotation, n=min(w.n, 3_000_000), bucket=w.bucket, tree=w.tree)
     shape = A.DEFAULT if args.no_tune else A.tuned(w.leaf, w.rotation, w.tree)
 
     def one_build(k):
