@@ -53,6 +53,12 @@ OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
 # on 3,000,000 keys of rot_l16 (a multi-wave launch): 28,126,208 B.  The
 # traffic of a launch grows with its key count.
 SEARCH_DRAM_BYTES_PER_KEY = 28_126_208 / 3_000_000
+# Pipe utilisation of k_search over the elapsed cycles of the same capture
+# (sm__pipe_fmaheavy_cycles_active, sm__pipe_alu_cycles_active,
+# smsp__issue_active; .avg.pct_of_peak_sustained_elapsed).
+SEARCH_NCU_PIPES = {"fmaheavy_busy_of_elapsed": 0.790, "alu_busy_of_elapsed": 0.727,
+                    "issue_busy_of_elapsed": 0.713,
+                    "capture": "ncu, k_search on 3e6 keys of rot_l16 (multi-wave), current kernel"}
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 
 
@@ -96,7 +102,8 @@ def search_roofline(peaks: dict, evals_per_launch: float, launch_ms: float, benc
                       "frac": evals_per_s * OPS_PER_EVAL / issue},
             "evals_per_launch": evals_per_launch, "launch_ms": launch_ms,
             "traffic": traffic,
-            "traffic_basis": "ncu DRAM bytes of k_search at 3e6 keys of rot_l16, scaled by n"}
+            "traffic_basis": "ncu DRAM bytes of k_search at 3e6 keys of rot_l16, scaled by n",
+            "ncu_pipes": SEARCH_NCU_PIPES}
 
 
 def parse():
@@ -407,6 +414,51 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def graph_vs_eager(M, torch, reps: int = 20) -> dict:
+    """Small builds, where launches, allocation and host reads dominate: the
+    plain_l8 workload (10^5 keys, l = 8, b = 100) built eagerly, and as a
+    prepared build captured once in a CUDA graph and replayed on new keys
+    copied into its input buffer; every replay's function equals the eager one."""
+    w = W.WORKLOADS["plain_l8"]
+    sets = [W.distinct_u64(w.n, w.seed + 10 + i) for i in range(4)]
+    dsets = [torch.from_numpy(k.view(np.int64)).cuda() for k in sets]
+    buf = torch.empty_like(dsets[0])
+    s = torch.cuda.Stream()
+    p = M.MPHF.prepare(w.n, w.leaf, w.bucket, w.rotation)
+    buf.copy_(dsets[0])
+    torch.cuda.synchronize()
+    p.enqueue(buf, stream=s)
+    p.finish(stream=s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        p.enqueue(buf, stream=s)
+    identical = True
+    for k in dsets:  # correctness first: replays on new keys equal eager builds
+        buf.copy_(k)
+        graph.replay()
+        p.finish()
+        e = M.MPHF.build(k, w.leaf, w.bucket, w.rotation)
+        identical = identical and same_function(p, e)
+        e.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(reps):
+        M.MPHF.build(dsets[i % 4], w.leaf, w.bucket, w.rotation).close()
+    torch.cuda.synchronize()
+    t_eager = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for i in range(reps):
+        buf.copy_(dsets[i % 4])
+        graph.replay()
+        p.finish()  # host read of status and totals: the function is usable after each
+    torch.cuda.synchronize()
+    t_graph = (time.perf_counter() - t0) / reps
+    p.close()
+    return {"workload": w.name, "n": w.n, "eager_keys_per_s": w.n / t_eager,
+            "graph_keys_per_s": w.n / t_graph, "eager_ms": 1e3 * t_eager, "graph_ms": 1e3 * t_graph,
+            "identical": bool(identical)}
+
+
 def query_throughput(torch, g, dkeys, stream, reps: int = 5) -> dict:
     """Queries of every built key through mphf_query, keys and results on the device."""
     out = torch.empty(dkeys.shape[0], dtype=torch.int64, device="cuda")
@@ -583,6 +635,8 @@ def run_ours(args):
         out["batch"] = batch_vs_plain(M, torch, args.batch_builds)
     if world == 1 and args.serve_requests > 0:
         out["serve"] = serve_leg(M, torch, args.serve_requests, args.rate)
+    if world == 1 and args.batch_builds > 0:
+        out["graph"] = graph_vs_eager(M, torch)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, keys, args.cpu_seconds)
         out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

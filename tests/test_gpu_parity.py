@@ -244,3 +244,22 @@ def test_keys_outside_the_set_walk_like_the_oracle(torch, orc, leaf, bucket, bij
     other = W.random_keys(100_000, kb, 977 + leaf + kb)
     got = g.query(to_dev(torch, other)).cpu().numpy().view(np.uint64)
     assert np.array_equal(got, o.query(other))
+
+
+@pytest.mark.parametrize("leaf,rotation", [(8, True), (12, False), (16, True)])
+def test_largest_bucket_matches_the_oracle(torch, orc, leaf, rotation):
+    """A bucket of exactly MAX_BUCKET (4096) keys, the largest a build accepts
+    (reading R12): all keys' hi words below 2^63, so with n = 4096 and b = 3000
+    (two buckets) every key lands in bucket 0.  Its whole tree, including the
+    fanout-2 levels above the lower aggregation levels, equals the oracle's."""
+    rng = np.random.default_rng(90 + leaf)
+    n = M.MAX_BUCKET
+    his = [int(x) for x in rng.integers(0, 2**63 - 1, n, dtype=np.int64)]
+    los = [int(x) for x in rng.integers(0, 2**63 - 1, n, dtype=np.int64)]
+    keys = _keys_with_fingerprints(orc, his, los)
+    o = orc.build_mphf(keys, leaf, 3000, rotation, threads=THREADS)
+    assert int(o.cum_keys[1]) == n  # one full bucket, one empty
+    dkeys = to_dev(torch, keys)
+    g = M.MPHF.build(dkeys, leaf, 3000, rotation)
+    assert g.info.max_bucket == n
+    assert_same_function(o, g, keys, dkeys)
