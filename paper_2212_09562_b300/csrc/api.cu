@@ -1646,6 +1646,11 @@ void server_control(mphf_server_t *S) {
                 S->pending.clear();
                 lk.unlock();
                 for (ServerRequest *r : left) finish(S, r, rc, nullptr);
+                // the search may still read the active requests' arrays: stop it first
+                set_stop(S, 1);
+                cudaStreamSynchronize(S->search);
+                cudaGetLastError();
+                running = false;
                 for (Active *a : active) {
                     if (a->job.h) fail_job(a->job, rc, c.mem);
                     release_active(c, *a);

@@ -1779,9 +1779,13 @@ void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nod
 // device: the sizes and word offsets of both sequences from the device totals
 // (the same ef_dims as the host), then the writers and the popcounts of the
 // second high-bit vector read them from there.
-__global__ void k_ef_plan(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, EfPlan *p) {
+__global__ void k_ef_plan(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb,
+                          uint64_t cap_bits, EfPlan *p) {
     if (blockIdx.x || threadIdx.x) return;
-    const EfDims a = ef_dims(nb + 1, cum_keys[nb]), b = ef_dims(nb + 1, bit_pos[nb]);
+    // a code longer than reserved was refused (k_gr_write); its Elias-Fano
+    // sizes would not fit the arrays sized for cap_bits either, so nothing is written
+    p->ok = bit_pos[nb] <= cap_bits;
+    const EfDims a = ef_dims(nb + 1, cum_keys[nb]), b = ef_dims(nb + 1, p->ok ? bit_pos[nb] : 0);
     p->L[0] = a.L;
     p->L[1] = b.L;
     p->off[0] = 0;                                      // low words of the key offsets
@@ -1794,6 +1798,7 @@ __global__ void k_ef_plan(const uint64_t *cum_keys, const uint64_t *bit_pos, uin
 
 __global__ void k_ef_write_plan(const uint64_t *v, uint64_t k, const EfPlan *p, uint32_t which,
                                 uint64_t *ef) {
+    if (!p->ok) return;
     const uint32_t L = p->L[which];
     uint64_t *low = ef + p->off[2 * which], *high = ef + p->off[2 * which + 1];
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < k;
@@ -1809,15 +1814,16 @@ __global__ void k_ef_write_plan(const uint64_t *v, uint64_t k, const EfPlan *p, 
 // (zero past its end: the buffer is zeroed up to the reserved size), out[max_words] = 0.
 __global__ void k_popcount_plan(const uint64_t *ef, const EfPlan *p, uint64_t max_words, uint64_t *out) {
     const uint64_t *high = ef + p->off[3];
-    const uint64_t words = p->high[1];
+    const uint64_t words = p->ok ? p->high[1] : 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= max_words;
          i += (uint64_t)gridDim.x * blockDim.x)
         out[i] = i < words ? __popcll(high[i]) : 0;
 }
 
-void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, EfPlan *p,
-                       uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp, cudaStream_t st) {
-    k_ef_plan<<<1, 32, 0, st>>>(cum_keys, bit_pos, nb, p);
+void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, uint64_t cap_bits,
+                       EfPlan *p, uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp,
+                       cudaStream_t st) {
+    k_ef_plan<<<1, 32, 0, st>>>(cum_keys, bit_pos, nb, cap_bits, p);
     k_ef_write_plan<<<grid_for(nb + 1, 256), 256, 0, st>>>(cum_keys, nb + 1, p, 0, ef);
     k_ef_write_plan<<<grid_for(nb + 1, 256), 256, 0, st>>>(bit_pos, nb + 1, p, 1, ef);
     k_popcount_plan<<<grid_for(max_high1 + 1, 256), 256, 0, st>>>(ef, p, max_high1, rank1);

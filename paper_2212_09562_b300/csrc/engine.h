@@ -144,6 +144,7 @@ void launch_stats(const uint64_t *values, const uint16_t *node_m, uint64_t n_nod
 // Elias-Fano of a prepared build (code length known only on the device): the
 // sizes and word offsets of both sequences, as ef_dims gives them.
 struct EfPlan {
+    uint32_t ok;       // the code fits the reserved length (else nothing is written)
     uint32_t L[2];
     uint64_t off[4];   // low and high words of the key offsets, then of the bit offsets
     uint64_t high[2];  // high words of each sequence
@@ -151,8 +152,9 @@ struct EfPlan {
 // Writes both sequences into the zeroed ef (sized for the largest possible
 // code), and rank1 = the rank directory of the bit offsets' high vector over
 // max_high1 words (tmp: scan_tmp_words(max_high1 + 1)).
-void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, EfPlan *p,
-                       uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp, cudaStream_t st);
+void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64_t nb, uint64_t cap_bits,
+                       EfPlan *p, uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp,
+                       cudaStream_t st);
 
 // Building one function on several GPUs (bucket ranges, Section 5.2).
 // Keys grouped by the rank owning their bucket (nb buckets, `world` ranges):

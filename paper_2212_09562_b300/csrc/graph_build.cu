@@ -257,7 +257,8 @@ int mphf_build_enqueue(mphf_t *h, const void *d_keys, void *stream) {
                     h->cum_keys, leaf, bij, h->gr, st, b.cap_bits, b.small);
     uint64_t *rank0 = h->ef_dir, *rank1 = rank0 + h->ef_dir_len[0];
     uint64_t *sel0 = rank1 + h->ef_dir_len[1], *sel1 = sel0 + h->ef_sel_len;
-    launch_ef_planned(h->cum_keys, h->bit_pos, nb, b.efp, h->ef, b.max_high1, rank1, b.scan_tmp, st);
+    launch_ef_planned(h->cum_keys, h->bit_pos, nb, b.cap_bits, b.efp, h->ef, b.max_high1, rank1,
+                      b.scan_tmp, st);
     launch_rank_dir(h->ef + e0.low_words, e0.high_words, rank0, b.scan_tmp, st);
     launch_select_dir(e0.high_words, rank0, sel0, st);
     launch_select_dir(b.max_high1, rank1, sel1, st);
