@@ -554,6 +554,7 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     step_ms, search_ms, evals, trials, my_evals, launches = [], [], 0, 0, 0, 0
+    leaf_k_trials, leaf_evals = 0, 0
     barrier()
     t_wall = time.perf_counter()
     for i in range(args.steps):
@@ -571,6 +572,8 @@ def run_ours(args):
         evals += sum(st[k][1] for k in ("leaf", "lower1", "lower2", "upper"))  # all ranks'
         trials += sum(st[k][0] for k in ("leaf", "lower1", "lower2", "upper"))
         my_evals += sum(mine[k][1] for k in ("leaf", "lower1", "lower2", "upper"))
+        leaf_k_trials += st["leaf"][0]
+        leaf_evals += st["leaf"][1]
         if i == args.steps - 1:
             bad = g.verify(dkeys)
             assert bad == 0, f"built function is not injective on this rank's keys ({bad} bad keys)"
@@ -628,6 +631,10 @@ def run_ours(args):
                                       f"{world} GPUs: one function of {world} x {w.n} keys in "
                                       "bucket-range shards (all-to-all of keys, all-gather of shards)")},
            "trials_per_s": trials / (total_ms / 1000.0),
+           # rotation fitting: one leaf trial is one k (m seeds k m + r at once); its
+           # plain-equivalent count is m per trial, which is the leaves' evaluation count
+           "leaf_trials": {"per_s": leaf_k_trials / (total_ms / 1000.0),
+                           "plain_equivalent_per_s": leaf_evals / (total_ms / 1000.0)},
            "evals_per_s": evals / (total_ms / 1000.0),
            "search_ms": mean_search, "wall_s": wall, "stage_ms": stages, "query": query,
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
