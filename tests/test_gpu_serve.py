@@ -198,3 +198,24 @@ def test_freed_request_slots_are_refilled(torch):
             same(res[t][1], M.MPHF.build(k, 8, 1000, True))
     finally:
         srv.close()
+
+
+def test_search_blocks_leave_after_their_wait_bound_and_the_server_recovers(torch):
+    """With a 1 ms bound on a serving-search block's wait for work, blocks
+    leave whenever the queue is empty for that long (between requests, and
+    while a request is being prepared); the server launches the search again
+    for the next work, and every result still equals its plain build."""
+    reqs = requests(torch, 6, 41)
+    srv = M.Server(max_requests=2, idle_ms=1)
+    try:
+        tickets = []
+        for dk, leaf in reqs:
+            tickets.append(srv.submit(dk, leaf, 500))
+            time.sleep(0.02)  # gaps longer than the bound
+        res = poll_all(srv, tickets)
+        for t, (dk, leaf) in zip(tickets, reqs):
+            st, built, _ = res[t]
+            assert st == M.OK
+            same(built, M.MPHF.build(dk, leaf, 500, True))
+    finally:
+        srv.close()
