@@ -347,6 +347,20 @@ void launch_scatter(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 // The search kernel.
 constexpr int STACK = 64;
 
+// The item a block works on, for sharing a node search's seed range with
+// idle blocks in the tail of a launch (full lower nodes only); q = nullptr:
+// no sharing (the serving search).
+struct HelpCtx {
+    StealQueue *q;
+    const uint32_t *bucket_head;
+    uint32_t nitems, inst, bucket;
+    uint32_t gbase, gpos;  // key offset within the bucket: of the item, of the node searched
+    uint64_t *glo;         // the build's grouped keys
+    uint64_t kbeg;         // the bucket's first key
+};
+constexpr uint32_t kStealReady = 1u << 31;
+constexpr uint32_t kHelpMarker = 0xFFFFFFFEu;  // a steal item inviting a block to a shared search
+
 struct BlockState {
     uint16_t st_off[STACK], st_m[STACK], st_pidx[STACK];
     uint8_t st_depth[STACK];
@@ -354,6 +368,8 @@ struct BlockState {
     uint32_t nleaves, leaf_next, flags, item;
     unsigned long long found, claim;
     int give;  // stack entries to give away now
+    uint32_t want, hround, hstop, hgen;  // shared node search: open it / round / stop / generation
+    HelpCtx hc;
     uint32_t cnt[16];
     unsigned long long lut64[16];  // child -> counter increment (last child: 0)
     uint32_t lut32[16];
@@ -463,38 +479,167 @@ constexpr int kKeyUnroll = 8;  // key-loop unroll factor of the split search
 // descriptor's spt: 2 by default where trials are many, the full nodes of
 // l = 16; 1 keeps the round, and the work past the winning seed, small
 // elsewhere; the autotuner may pick another per device).
+// The counters of one round: seeds s0 + j T (j < SPT) over the node's keys.
 template <int SPT, class Cnt, class Mod, class Div>
-__device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div,
-                                                 const Cnt *lut, Cnt expected, const Mixer &mx,
-                                                 uint64_t maxv, bool &limit, BlockState &S) {
+__device__ __forceinline__ void round_counts(const uint64_t *xs, uint32_t m, Mod mod, Div div,
+                                             const Cnt *lut, const Mixer &mx, uint64_t s0,
+                                             Cnt (&cnt)[SPT]) {
     const uint32_t T = blockDim.x;
-    for (uint64_t base = 0;; base += (uint64_t)T * SPT) {
-        Cnt cnt[SPT];
 #pragma unroll
-        for (int j = 0; j < SPT; j++) cnt[j] = 0;
-        const uint64_t s0 = base + threadIdx.x;
-        auto eval = [&](uint64_t x) {
+    for (int j = 0; j < SPT; j++) cnt[j] = 0;
+    auto eval = [&](uint64_t x) {
 #pragma unroll
-            for (int j = 0; j < SPT; j++) {
-                uint32_t hl, hh;
-                mx(x + s0 + (uint64_t)j * T, hl, hh);
-                cnt[j] += lut[div(mod_halves(mod, hl, hh))];
-            }
-        };
-        // xs is 16-byte aligned: two keys per shared-memory load
-        const ulonglong2 *xs2 = (const ulonglong2 *)xs;
-#pragma unroll kKeyUnroll
-        for (uint32_t i = 0; i < m / 2; i++) {
-            const ulonglong2 q = xs2[i];
-            eval(q.x);
-            eval(q.y);
+        for (int j = 0; j < SPT; j++) {
+            uint32_t hl, hh;
+            mx(x + s0 + (uint64_t)j * T, hl, hh);
+            cnt[j] += lut[div(mod_halves(mod, hl, hh))];
         }
-        if (m & 1) eval(xs[m - 1]);
+    };
+    // xs is 16-byte aligned: two keys per shared-memory load
+    const ulonglong2 *xs2 = (const ulonglong2 *)xs;
+#pragma unroll kKeyUnroll
+    for (uint32_t i = 0; i < m / 2; i++) {
+        const ulonglong2 q = xs2[i];
+        eval(q.x);
+        eval(q.y);
+    }
+    if (m & 1) eval(xs[m - 1]);
+}
+
+
+// Thread 0: share the current node search now (idle blocks wait, no bucket left).
+__device__ __forceinline__ bool help_wanted(const HelpCtx &h) {
+    return h.q && blockIdx.x < kHelpCap && atomicAdd(&h.q->idle, 0u) > 0 &&
+           atomicAdd((unsigned int *)h.bucket_head, 0u) >= h.nitems;
+}
+
+// Rounds of the shared search of node `rec`, claimed in order by the owner
+// and any helpers: a round whose first seed is above the best found so far,
+// or above maxv, is not evaluated (it cannot hold the smallest), and a block
+// stops at the first such round.  Every round below the best round was
+// claimed before it and is evaluated by its claimer, so once all blocks have
+// left, rec->best is the smallest valid seed.
+template <int SPT, class Cnt, class Mod, class Div>
+__device__ __forceinline__ void shared_rounds(const uint64_t *xs, uint32_t m, Mod mod, Div div, const Cnt *lut,
+                                           Cnt expected, uint64_t maxv, HelpRec *rec, uint32_t gen,
+                                           bool owner, BlockState &S) {
+    const uint32_t T = blockDim.x;
+    const uint64_t step = (uint64_t)T * SPT;
+    const Mixer mx{};
+    for (;;) {
+        if (threadIdx.x == 0) {
+            bool stop = false;
+            uint32_t r = 0;
+            if (!owner && (atomicAdd(&rec->state, 0u) != 1u || atomicAdd(&rec->gen, 0u) != gen)) {
+                stop = true;
+            } else {
+                r = atomicAdd(&rec->next_round, 1u);
+                const unsigned long long b = atomicAdd(&rec->best, 0ull);
+                const uint64_t first = (uint64_t)r * step;
+                stop = first > b || first > maxv;
+            }
+            S.hround = r;
+            S.hstop = stop;
+        }
+        __syncthreads();
+        if (S.hstop) break;
+        const uint64_t s0 = (uint64_t)S.hround * step + threadIdx.x;
+        Cnt cnt[SPT];
+        round_counts<SPT>(xs, m, mod, div, lut, mx, s0, cnt);
         uint64_t best = ~0ull;
 #pragma unroll
         for (int j = SPT - 1; j >= 0; j--)
             if (cnt[j] == expected && s0 + (uint64_t)j * T <= maxv) best = s0 + (uint64_t)j * T;
         const bool ok = best != ~0ull;
+        if (__syncthreads_or(ok) && ok) atomicMin(&rec->best, (unsigned long long)best);
+    }
+    __syncthreads();
+}
+
+// The owner opens its node to helpers from round `first` on: the node's
+// salted keys go to the build's grouped-key array at the node's place (a
+// helper copies them from there), then the record, then a few help items in
+// the steal queue for the idle blocks.  After its last round it closes the
+// record, waits (bounded) for the helpers to leave and takes the best seed.
+template <int SPT, class Cnt, class Mod, class Div>
+__device__ __forceinline__ uint64_t open_help(const uint64_t *xs, uint32_t m, Mod mod, Div div, const Cnt *lut,
+                                           Cnt expected, uint64_t maxv, bool &limit, BlockState &S,
+                                           const HelpCtx &h, uint32_t first) {
+    HelpRec *rec = &help_recs(h.q)[blockIdx.x];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) h.glo[h.kbeg + h.gpos + i] = xs[i];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        rec->inst = h.inst;
+        rec->bucket = h.bucket;
+        rec->gpos = h.gpos;
+        rec->m = m;
+        rec->best = ~0ull;
+        rec->next_round = first;
+        const uint32_t gen = atomicAdd(&rec->gen, 0u);
+        S.hgen = gen;
+        __threadfence();
+        atomicExch(&rec->state, 1u);
+        uint32_t want = atomicAdd(&h.q->idle, 0u);
+        want = want > 16 ? 16 : want;
+        for (uint32_t k = 0; k < want; k++) {  // invitations: (marker, owner block, generation)
+            const uint32_t slot = atomicAdd(&h.q->tail, 1u);
+            if (slot >= kStealCap) break;
+            unsigned int *w = h.q->items[slot].w;
+            __stcg(w + 0, kHelpMarker);
+            __stcg(w + 1, blockIdx.x);
+            __stcg(w + 2, gen);
+            __threadfence();
+            atomicExch(w + 3, kStealReady);
+        }
+    }
+    __syncthreads();
+    shared_rounds<SPT>(xs, m, mod, div, lut, expected, maxv, rec, S.hgen, true, S);
+    if (threadIdx.x == 0) {
+        atomicExch(&rec->state, 2u);
+        __threadfence();
+        unsigned long long t0, now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        while (atomicAdd(&rec->helpers, 0u) != 0) {  // helpers finish their round and leave
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            if (now - t0 > 10000000000ull) {  // 10 s: cannot happen unless the device misbehaves
+                S.flags |= ST_TIMEOUT;
+                break;
+            }
+            __nanosleep(1000);
+        }
+        __threadfence();
+        S.found = atomicAdd(&rec->best, 0ull);
+        atomicAdd(&rec->gen, 1u);
+        atomicExch(&rec->state, 0u);
+    }
+    __syncthreads();
+    const uint64_t x = S.found;
+    if (x == ~0ull) {
+        limit = true;
+        return 0;
+    }
+    return x;
+}
+
+template <int SPT, class Cnt, class Mod, class Div>
+__device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m, Mod mod, Div div,
+                                                 const Cnt *lut, Cnt expected, const Mixer &mx,
+                                                 uint64_t maxv, bool &limit, BlockState &S,
+                                                 bool share = false) {
+    const uint32_t T = blockDim.x;
+    if (threadIdx.x == 0) S.want = 0;  // read after the first round's barrier
+    uint32_t round = 0;
+    for (uint64_t base = 0;; base += (uint64_t)T * SPT, round++) {
+        Cnt cnt[SPT];
+        const uint64_t s0 = base + threadIdx.x;
+        round_counts<SPT>(xs, m, mod, div, lut, mx, s0, cnt);
+        uint64_t best = ~0ull;
+#pragma unroll
+        for (int j = SPT - 1; j >= 0; j--)
+            if (cnt[j] == expected && s0 + (uint64_t)j * T <= maxv) best = s0 + (uint64_t)j * T;
+        const bool ok = best != ~0ull;
+        if (share && threadIdx.x == 0 && (round & 7) == 7) S.want = help_wanted(S.hc);
         if (__syncthreads_or(ok)) {
             if (ok) atomicMin(&S.found, (unsigned long long)best);
             __syncthreads();
@@ -504,6 +649,8 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
             limit = true;
             return 0;
         }
+        if (share && S.want)  // from the next round on, with the idle blocks
+            return open_help<SPT>(xs, m, mod, div, lut, expected, maxv, limit, S, S.hc, round + 1);
     }
 }
 
@@ -994,6 +1141,21 @@ __device__ __forceinline__ bool block_has_duplicate(const uint64_t *lo, uint32_t
     return __syncthreads_or(dup);
 }
 
+// The packed child counters of a lower node of m keys (see search_lower):
+// the per-child increments in S.lut32 / S.lut64 and the expected word.
+__device__ __forceinline__ uint64_t lower_counters(const Shape &sh, uint32_t m, BlockState &S) {
+    const uint32_t np = num_parts(sh, m);
+    const uint32_t w = field_width(lower_unit(sh, m));
+    uint64_t expected = 0;
+    for (uint32_t c = 0; c + 1 < np; c++) expected += (uint64_t)part_size(sh, m, c) << (w * c);
+    if (threadIdx.x < 16) {
+        const uint64_t inc = threadIdx.x + 1 < np ? 1ull << (w * threadIdx.x) : 0;
+        S.lut64[threadIdx.x] = inc;
+        S.lut32[threadIdx.x] = (uint32_t)inc;
+    }
+    return expected;
+}
+
 // One inner node (Section 2.2, "Splitting Trees"; Section 5.3, "Splittings":
 // a thread block tries seeds, then regroups the node's keys): search its
 // smallest valid seed, store it in preorder, regroup its keys by child in
@@ -1020,14 +1182,10 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
     } else {
         const uint32_t unit = lower_unit(sh, m);
         const uint32_t w = field_width(unit);
-        uint64_t expected = 0;
-        for (uint32_t c = 0; c + 1 < np; c++) expected += (uint64_t)part_size(sh, m, c) << (w * c);
-        if (tid < 16) {
-            uint64_t inc = tid + 1 < np ? 1ull << (w * tid) : 0;
-            S.lut64[tid] = inc;
-            S.lut32[tid] = (uint32_t)inc;
-        }
+        const uint64_t expected = lower_counters(sh, m, S);
+        if (tid == 0) S.hc.gpos = S.hc.gbase + off;  // where the node's keys sit in the bucket
         __syncthreads();
+        const bool share = S.hc.q != nullptr;
         bool done = false;
         if constexpr (LEAF != 0) {
             // full lower-1 and lower-2 nodes: compile-time modulus, unit, counter width
@@ -1042,16 +1200,16 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             if (m == L1) {
                 const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
                 const auto mod = make_modct<L1>(d.red[1]);
-                x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S)
-                  : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S)
-                               : search_lower<1, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S);
+                x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S, share)
+                  : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S, share)
+                               : search_lower<1, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S, share);
                 done = true;
             } else if (m == L2) {
                 const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
                 const auto mod = make_modct<L2>(d.red[2]);
-                x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S)
-                  : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S)
-                               : search_lower<1, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S);
+                x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S, share)
+                  : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S, share)
+                               : search_lower<1, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S, share);
                 done = true;
             }
         }
@@ -1214,8 +1372,6 @@ struct StealCtx {
     const uint32_t *bucket_head;
     uint32_t nitems, cap;
 };
-constexpr uint32_t kStealReady = 1u << 31;
-
 // Thread 0: the number of bottom stack entries to give away now.
 __device__ __forceinline__ int donation(const StealCtx &X, const BlockState &S) {
     if (!X.q || S.sp < 2) return 0;
@@ -1294,6 +1450,7 @@ __device__ __forceinline__ void process_item(const InstDesc &d, uint32_t inst, u
         S.nleaves = 0;
         S.leaf_next = 0;
         S.flags = 0;
+        S.hc = HelpCtx{X.q, X.bucket_head, X.nitems, inst, bucket, goff, goff, (uint64_t *)d.lo, kbeg};
         if (m0 <= sh.leaf) {
             A.leaf_off[0] = 0;
             A.leaf_m[0] = (uint8_t)m0;
@@ -1330,6 +1487,44 @@ __device__ __forceinline__ void process_bucket(const InstDesc &d, uint32_t bucke
                                                BlockState &S) {
     const uint32_t m = (uint32_t)(__ldcg(d.bucket_off + bucket + 1) - __ldcg(d.bucket_off + bucket));
     process_item<LEAF>(d, 0, bucket, 0, m > 4096 ? 4097u : m, 0, 0, A, S, StealCtx{nullptr, nullptr, 0, 0});
+}
+
+// A helper's part of a shared node search (open_help): the node's salted
+// keys from the build's grouped-key array, the same counters, modulus and
+// seeds per thread as the owner, then rounds until the owner's search ends.
+template <int LEAF>
+__device__ __forceinline__ void help_node(const InstDesc &d, HelpRec *rec, uint32_t gen,
+                                          const SmemArrays &A, BlockState &S) {
+    if constexpr (LEAF != 0) {
+        const Shape sh = make_shape((uint32_t)LEAF, d.tree);
+        const uint32_t m = __ldcg(&rec->m), bucket = __ldcg(&rec->bucket), gpos = __ldcg(&rec->gpos);
+        const uint64_t kbeg = __ldcg(d.bucket_off + bucket);
+        for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) A.tlo[i] = __ldcg(d.lo + kbeg + gpos + i);
+        const uint64_t expected = lower_counters(sh, m, S);
+        __syncthreads();
+        constexpr uint32_t f1 = ((35u * LEAF + 154u) / 100u) < 2 ? 2 : (35u * LEAF + 154u) / 100u;
+        constexpr uint32_t f2 = ((21u * LEAF + 189u) / 100u) < 2 ? 2 : (21u * LEAF + 189u) / 100u;
+        constexpr uint32_t L1 = f1 * LEAF, L2 = f2 * L1;
+        constexpr bool n1 = counter_fits32(L1, field_width(LEAF), f1);
+        constexpr bool n2 = counter_fits32(L2, field_width(L1), f2);
+        using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
+        using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
+        const uint64_t *xs = A.tlo;
+        if (d.tree == MPHF_TREE_RECSPLIT && m == L1) {
+            const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
+            const auto mod = make_modct<L1>(d.red[1]);
+            if (d.spt == 4) shared_rounds<4>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, d.max_value, rec, gen, false, S);
+            else if (d.spt == 2) shared_rounds<2>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, d.max_value, rec, gen, false, S);
+            else shared_rounds<1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, d.max_value, rec, gen, false, S);
+        } else if (d.tree == MPHF_TREE_RECSPLIT && m == L2) {
+            const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
+            const auto mod = make_modct<L2>(d.red[2]);
+            if (d.spt == 4) shared_rounds<4>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, d.max_value, rec, gen, false, S);
+            else if (d.spt == 2) shared_rounds<2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, d.max_value, rec, gen, false, S);
+            else shared_rounds<1>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, d.max_value, rec, gen, false, S);
+        }
+    }
+    __syncthreads();
 }
 
 // Thread 0 of an idle block: a node from the steal queue, or ~0u when the
@@ -1437,11 +1632,36 @@ __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, uint32_t 
                 const uint64_t mm = __ldcg(dd.bucket_off + bucket + 1) - __ldcg(dd.bucket_off + bucket);
                 m0 = mm > 4096 ? 4097u : (uint32_t)mm;
             }
-        } else if (got != ~0ull) {  // a subtree another block gave away
+        } else if (got != ~0ull) {  // a subtree another block gave away, or an invitation
             const unsigned int *w = steal->items[got].w;
             inst = __ldcg(w + 0);
             bucket = __ldcg(w + 1);
             const uint32_t w2 = __ldcg(w + 2), w3 = __ldcg(w + 3);
+            if (inst == kHelpMarker) {  // join block w1's search of one node, generation w2
+                HelpRec *rec = &help_recs(steal)[bucket];
+                if (threadIdx.x == 0) {
+                    atomicAdd(&rec->helpers, 1u);
+                    __threadfence();
+                    S.hstop = !(atomicAdd(&rec->state, 0u) == 1u && atomicAdd(&rec->gen, 0u) == w2);
+                }
+                __syncthreads();
+                if (!S.hstop) {
+                    const InstDesc d = insts[__ldcg(&rec->inst)];
+                    switch (d.leaf) {
+                        case 8: help_node<8>(d, rec, w2, A, S); break;
+                        case 12: help_node<12>(d, rec, w2, A, S); break;
+                        case 16: help_node<16>(d, rec, w2, A, S); break;
+                        default: break;
+                    }
+                }
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    atomicSub(&rec->helpers, 1u);
+                    atomicSub(&steal->busy, 1u);
+                }
+                __syncthreads();
+                continue;
+            }
             goff = w2 & 0xFFFFu;
             m0 = w2 >> 16;
             pidx = w3 & 0xFFFFu;

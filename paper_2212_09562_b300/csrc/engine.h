@@ -107,10 +107,26 @@ struct StealItem {
 };
 struct StealQueue {
     unsigned int tail, head, idle, busy;
-    StealItem items[1];  // kStealCap entries
+    StealItem items[1];  // kStealCap entries, then kHelpCap HelpRec (help_recs())
+};
+// A node search shared with idle blocks by seed range (see k_search): rounds
+// of blockDim * seeds-per-thread consecutive seeds are claimed in order from
+// next_round; the smallest valid seed any block finds goes to best.
+struct HelpRec {
+    unsigned int state;       // 0 closed, 1 open to helpers, 2 closing
+    unsigned int helpers;     // helper blocks inside the search
+    unsigned int gen;         // raised at every closing
+    unsigned int next_round;
+    unsigned int inst, bucket, gpos, m;  // the node: build, bucket, key offset in the bucket, size
+    unsigned long long best;
 };
 constexpr uint32_t kStealCap = 32768;
-constexpr size_t kStealBytes = 16 + sizeof(StealItem) * kStealCap;
+constexpr uint32_t kHelpCap = 4096;  // one record per block of the launch (more blocks: no sharing)
+constexpr size_t kStealItemsEnd = 16 + sizeof(StealItem) * kStealCap;
+constexpr size_t kStealBytes = kStealItemsEnd + sizeof(HelpRec) * kHelpCap;
+__host__ __device__ inline HelpRec *help_recs(StealQueue *q) {
+    return (HelpRec *)((char *)q + kStealItemsEnd);
+}
 void launch_search(const InstDesc *d_inst, uint32_t ninst, const WorkItem *d_items, uint32_t items,
                    uint32_t *d_head, const SearchLaunch &L, StealQueue *steal, cudaStream_t st);
 // The serving search (reads work from a ring the host appends to; see k_serve).
