@@ -328,25 +328,41 @@ void fail_job(Job &j, int rc, Mem &mem) {
 // Scratch shared by the jobs of one engine pass: the prefix-sum scratch, the
 // bucket-size histogram of the work order, and a pinned host buffer for the
 // totals read between phases (four words per job).
+// Pinned host words for the totals read between phases, one buffer per host
+// thread, kept for the thread's life: cudaMallocHost / cudaFreeHost cost
+// about as much as a whole small build, and cudaFreeHost synchronises.
+struct PinnedWords {
+    uint64_t *p = nullptr;
+    size_t words = 0;
+    ~PinnedWords() {
+        if (p) cudaFreeHost(p);
+    }
+    uint64_t *get(size_t n) {
+        if (n <= words) return p;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        words = 0;
+        if (cudaMallocHost(&p, n * 8) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return nullptr;
+        }
+        words = n;
+        return p;
+    }
+};
+thread_local PinnedWords t_pinned;
+
 struct EngineCtx {
     Mem mem;
     uint64_t *host = nullptr, *scan_tmp = nullptr, *size_hist = nullptr;
     uint32_t *size_cursor = nullptr;
-    size_t cap_jobs = 0;
     uint64_t cap_nb = 0;
 
     // Room for `jobs` jobs of at most max_nb buckets each.
     int reserve(size_t jobs, uint64_t max_nb) {
-        if (jobs > cap_jobs) {
-            if (host) cudaFreeHost(host);
-            host = nullptr;
-            cap_jobs = 0;
-            if (cudaMallocHost(&host, 8 * 4 * (jobs ? jobs : 1)) != cudaSuccess) {
-                cudaGetLastError();
-                return MPHF_ECUDA;
-            }
-            cap_jobs = jobs;
-        }
+        host = t_pinned.get(4 * (jobs ? jobs : 1));
+        if (!host) return MPHF_ECUDA;
         if (!scan_tmp || max_nb > cap_nb) {
             mem.put(scan_tmp);
             const uint64_t len = max_nb + 2 > 4098 ? max_nb + 2 : 4098;
@@ -373,9 +389,7 @@ struct EngineCtx {
         scan_tmp = size_hist = nullptr;
         size_cursor = nullptr;
         cudaStreamSynchronize(mem.st);
-        if (host) cudaFreeHost(host);
-        host = nullptr;
-        cap_jobs = 0;
+        host = nullptr;  // the thread's pinned words stay for its next build
         cap_nb = 0;
     }
 };

@@ -639,7 +639,11 @@ __device__ __forceinline__ uint64_t search_lower(const uint64_t *xs, uint32_t m,
         for (int j = SPT - 1; j >= 0; j--)
             if (cnt[j] == expected && s0 + (uint64_t)j * T <= maxv) best = s0 + (uint64_t)j * T;
         const bool ok = best != ~0ull;
-        if (share && threadIdx.x == 0 && (round & 7) == 7) S.want = help_wanted(S.hc);
+        // shared only once a search has run a while, and only where a round is long
+        // (at least 2^16 evaluations): the per-round claim would not pay below that
+        if (share && threadIdx.x == 0 && (round & 7) == 7 && round >= 15 &&
+            (uint64_t)T * SPT * m >= (1u << 16))
+            S.want = help_wanted(S.hc);
         if (__syncthreads_or(ok)) {
             if (ok) atomicMin(&S.found, (unsigned long long)best);
             __syncthreads();
