@@ -9,24 +9,25 @@
 //   -> Golomb-Rice bits, Elias-Fano sequences, rank directories, statistics.
 // The two host reads size the output buffers; the build returns after a
 // final stream synchronisation with the device status mapped to an error.
+//
+// This file holds the per-device tables, the engine's phases (build_engine.h),
+// builds, batches, queries, verification, serialisation and loading.  The
+// sharded-build entry points are in shard.cu, the prepared (graph-capturable)
+// build in graph_build.cu, the server in serve.cu.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
-#include <chrono>
-#include <condition_variable>
-#include <deque>
 #include <map>
 #include <mutex>
 #include <new>
-#include <thread>
-#include <unordered_map>
 #include <vector>
 
+#include "build_engine.h"
 #include "common.cuh"
 #include "engine.h"
-#include "mphf.h"
 #include "handle.h"
+#include "mphf.h"
 #include "tables.h"
 
 using namespace rs;
@@ -255,27 +256,10 @@ int mphf_tau_table(uint32_t leaf_size, uint32_t leaf_bijection, uint32_t tree_sh
 // same phases on one stream, with one host read between phases for all of
 // them and ONE persistent search launch over the buckets of every job
 // (largest buckets first across jobs, mixed leaf sizes in the same launch).
-namespace {
+namespace rs {
 
-struct Job {
-    const void *d_keys = nullptr;
-    uint64_t n = 0;
-    mphf_build_params p{};
-    mphf_t *h = nullptr;
-    int rc = MPHF_OK;
-    uint64_t nb = 0, maxv = 0;
-    BucketRange range{0, 0};  // the buckets this job builds (all of them unless a shard)
-    uint64_t *lo_s = nullptr, *counters = nullptr;
-    uint8_t *bb_s = nullptr;
-    uint32_t *cursor = nullptr, *small = nullptr;  // small: status, max bucket, spare
-    uint32_t *blk = nullptr;                         // per-block bucket counts (two-level sort)
-    uint32_t sort_g = 0;
-    uint16_t *node_m = nullptr;
-    uint64_t n_nodes = 0;
-    uint32_t max_m = 0;    // largest bucket
-    bool planned = false;  // its buckets are counted in the pass's work-order histogram
-    InstDesc desc{};       // what the search kernel reads about this job
-};
+thread_local PinnedWords t_pinned;
+
 
 // Parameters of a build apart from where its keys are.
 int check_shape(uint64_t n, const mphf_build_params *p) {
@@ -324,75 +308,6 @@ void fail_job(Job &j, int rc, Mem &mem) {
         j.h = nullptr;
     }
 }
-
-// Scratch shared by the jobs of one engine pass: the prefix-sum scratch, the
-// bucket-size histogram of the work order, and a pinned host buffer for the
-// totals read between phases (four words per job).
-// Pinned host words for the totals read between phases, one buffer per host
-// thread, kept for the thread's life: cudaMallocHost / cudaFreeHost cost
-// about as much as a whole small build, and cudaFreeHost synchronises.
-struct PinnedWords {
-    uint64_t *p = nullptr;
-    size_t words = 0;
-    ~PinnedWords() {
-        if (p) cudaFreeHost(p);
-    }
-    uint64_t *get(size_t n) {
-        if (n <= words) return p;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        words = 0;
-        if (cudaMallocHost(&p, n * 8) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return nullptr;
-        }
-        words = n;
-        return p;
-    }
-};
-thread_local PinnedWords t_pinned;
-
-struct EngineCtx {
-    Mem mem;
-    uint64_t *host = nullptr, *scan_tmp = nullptr, *size_hist = nullptr;
-    uint32_t *size_cursor = nullptr;
-    uint64_t cap_nb = 0;
-
-    // Room for `jobs` jobs of at most max_nb buckets each.
-    int reserve(size_t jobs, uint64_t max_nb) {
-        host = t_pinned.get(4 * (jobs ? jobs : 1));
-        if (!host) return MPHF_ECUDA;
-        if (!scan_tmp || max_nb > cap_nb) {
-            mem.put(scan_tmp);
-            const uint64_t len = max_nb + 2 > 4098 ? max_nb + 2 : 4098;
-            scan_tmp = (uint64_t *)mem.get((scan_tmp_words(len) + 64) * 8);
-            cap_nb = max_nb;
-        }
-        if (!size_hist) size_hist = (uint64_t *)mem.get(4098 * 8);
-        if (!size_cursor) size_cursor = (uint32_t *)mem.get(4097 * 4);
-        return scan_tmp && size_hist && size_cursor ? MPHF_OK : MPHF_ENOMEM;
-    }
-    // The work-order histogram starts empty for every pass.
-    int clear_order() {
-        if (cudaMemsetAsync(size_hist, 0, 4098 * 8, mem.st) != cudaSuccess ||
-            cudaMemsetAsync(size_cursor, 0, 4097 * 4, mem.st) != cudaSuccess) {
-            cudaGetLastError();
-            return MPHF_ECUDA;
-        }
-        return MPHF_OK;
-    }
-    void release() {
-        mem.put(scan_tmp);
-        mem.put(size_hist);
-        mem.put(size_cursor);
-        scan_tmp = size_hist = nullptr;
-        size_cursor = nullptr;
-        cudaStreamSynchronize(mem.st);
-        host = nullptr;  // the thread's pinned words stay for its next build
-        cap_nb = 0;
-    }
-};
 
 #define CU(x)                     \
     do {                          \
@@ -729,7 +644,7 @@ void start_job(Job &j, const void *d_keys, uint64_t n, const mphf_build_params &
     }
 }
 
-}  // namespace
+}  // namespace rs
 
 extern "C" {
 
@@ -774,262 +689,6 @@ int mphf_build_host(const void *h_keys, uint64_t n, const mphf_build_params *p, 
     rc = mphf_build_ex(d, n, p, stream, out);
     mem.put(d);
     return rc;
-}
-
-// ---------------------------------------------------------------------------
-// One function built on several GPUs (Section 5.2: consecutive bucket
-// ranges, local sequences concatenated).  Rank r of `world` owns buckets
-// [floor(r nb / world), floor((r + 1) nb / world)) of the function over
-// n_total keys (nb = ceil(n_total / bucket_size)).
-
-// The pack of a shard: kShardHead header words, then its arrays.
-constexpr size_t kShardHead = 24;
-constexpr uint64_t kShardMagic = 0x3144485346504D52ull;  // "RMPFSHD1"
-
-static void shard_range(uint64_t nb, uint32_t rank, uint32_t world, uint64_t *lo, uint64_t *hi) {
-    *lo = nb * rank / world;
-    *hi = nb * (rank + 1) / world;
-}
-
-int mphf_build_shard(const void *d_keys, uint64_t n, uint64_t n_total, const mphf_build_params *p,
-                     uint32_t rank, uint32_t world, void *stream, mphf_t **out) {
-    if (!out || !p) return MPHF_EINVAL;
-    *out = nullptr;
-    if (world == 0 || world > MPHF_MAX_SHARDS || rank >= world || n > n_total) return MPHF_EINVAL;
-    int rc = check_shape(n_total, p);
-    if (rc != MPHF_OK) return rc;
-    std::vector<Job> jobs(1);
-    Job &j = jobs[0];
-    start_job(j, d_keys, n, *p);
-    if (j.rc) return j.rc;
-    const uint64_t nb_hash = (n_total + p->bucket_size - 1) / p->bucket_size;
-    uint64_t b_lo, b_hi;
-    shard_range(nb_hash, rank, world, &b_lo, &b_hi);
-    j.nb = b_hi - b_lo;
-    j.range = BucketRange{nb_hash, b_lo};
-    j.h->info.nb = j.nb;
-    j.h->shard = true;
-    j.h->b_lo = b_lo;
-    j.h->nb_hash = nb_hash;
-    j.h->n_total = n_total;
-    int grc = run_jobs(jobs, (cudaStream_t)stream, p->allocator, p->threads_per_block, p->blocks_per_sm);
-    if (grc) return grc;
-    if (j.rc) return j.rc;
-    *out = j.h;
-    return MPHF_OK;
-}
-
-int mphf_shard_route(const void *d_keys, uint64_t n, uint32_t key_bytes, uint64_t n_total,
-                     uint32_t bucket_size, uint32_t world, void *d_out, uint64_t *h_counts,
-                     void *stream) {
-    if (!h_counts || world == 0 || world > MPHF_MAX_SHARDS || (key_bytes != 8 && key_bytes != 16) ||
-        bucket_size < 1 || bucket_size > MPHF_MAX_BUCKET_SIZE || n > n_total || n_total >= (1ull << 32))
-        return MPHF_EINVAL;
-    if (n > 0 && (!d_keys || !d_out || ((uintptr_t)d_keys & 7) || ((uintptr_t)d_out & 7)))
-        return MPHF_EINVAL;
-    memset(h_counts, 0, world * sizeof(uint64_t));
-    if (n == 0) return MPHF_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const uint64_t nb = (n_total + bucket_size - 1) / bucket_size;
-    Mem mem{nullptr, st};
-    uint64_t *d = (uint64_t *)mem.get(2 * world * sizeof(uint64_t));
-    if (!d) return MPHF_ENOMEM;
-    std::vector<uint64_t> cur(world);
-    int rc = MPHF_OK;
-    if (cudaMemsetAsync(d, 0, world * sizeof(uint64_t), st) != cudaSuccess) rc = MPHF_ECUDA;
-    if (rc == MPHF_OK) {
-        launch_route_count((const uint64_t *)d_keys, n, key_bytes, nb, world, d, st);
-        if (cudaMemcpyAsync(h_counts, d, world * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
-            rc = MPHF_ECUDA;
-    }
-    if (rc == MPHF_OK) {
-        uint64_t run = 0;
-        for (uint32_t r = 0; r < world; r++) {
-            cur[r] = run;
-            run += h_counts[r];
-        }
-        if (cudaMemcpyAsync(d + world, cur.data(), world * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
-            rc = MPHF_ECUDA;
-        else
-            launch_route_scatter((const uint64_t *)d_keys, n, key_bytes, nb, world, d + world,
-                                 (uint64_t *)d_out, st);
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
-            rc = MPHF_ECUDA;
-    }
-    if (rc != MPHF_OK) cudaGetLastError();
-    mem.put(d);
-    cudaStreamSynchronize(st);
-    return rc;
-}
-
-static size_t shard_pack_bytes(const mphf_t *h) {
-    const uint64_t nb = h->info.nb;
-    return 8 * (kShardHead + 3 * (nb + 1) + h->info.n_nodes + h->info.gr_words);
-}
-
-int mphf_shard_pack(const mphf_t *h, void *d_buf, size_t *len, void *stream) {
-    if (!h || !len || !h->shard) return MPHF_EINVAL;
-    const size_t need = shard_pack_bytes(h);
-    if (!d_buf) {
-        *len = need;
-        return MPHF_OK;
-    }
-    if (*len < need || ((uintptr_t)d_buf & 7)) {
-        *len = need;
-        return MPHF_EINVAL;
-    }
-    const mphf_info &I = h->info;
-    uint64_t hd[kShardHead] = {kShardMagic, I.n, I.nb, h->b_lo, h->n_total, I.n_nodes, I.gr_bits,
-                               I.leaf_size | ((uint64_t)I.tree_shape << 16), I.bucket_size,
-                               I.key_bytes, I.leaf_bijection, I.max_bucket, 0, 0, 0, 0};
-    for (int k = 0; k < 4; k++) {
-        hd[16 + k] = h->stats.trials[k];
-        hd[20 + k] = h->stats.evals[k];
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    uint64_t *w = (uint64_t *)d_buf;
-    const uint64_t nb = I.nb;
-    struct Part {
-        const void *src;
-        size_t words;
-    } parts[] = {{hd, kShardHead}, {h->cum_keys, nb + 1}, {h->node_off, nb + 1},
-                 {h->bit_pos, nb + 1}, {h->values, I.n_nodes}, {h->gr, I.gr_words}};
-    int rc = MPHF_OK;
-    for (const Part &q : parts) {
-        if (q.words && cudaMemcpyAsync(w, q.src, q.words * 8, cudaMemcpyDefault, st) != cudaSuccess)
-            rc = MPHF_ECUDA;
-        w += q.words;
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess) rc = MPHF_ECUDA;  // hd is read by the copy
-    if (rc != MPHF_OK) cudaGetLastError();
-    *len = need;
-    return rc;
-}
-
-int mphf_shard_concat(const void *const *d_parts, const size_t *lens, uint32_t count,
-                      const mphf_allocator *allocator, void *stream, mphf_t **out) {
-    if (!out || !d_parts || !lens || count == 0 || count > MPHF_MAX_SHARDS) return MPHF_EINVAL;
-    *out = nullptr;
-    cudaStream_t st = (cudaStream_t)stream;
-    std::vector<uint64_t> hd(kShardHead * (size_t)count);
-    for (uint32_t s = 0; s < count; s++) {
-        if (!d_parts[s] || ((uintptr_t)d_parts[s] & 7) || lens[s] < kShardHead * 8) return MPHF_EINVAL;
-        if (cudaMemcpyAsync(&hd[kShardHead * s], d_parts[s], kShardHead * 8, cudaMemcpyDefault, st) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return MPHF_ECUDA;
-        }
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaGetLastError();
-        return MPHF_ECUDA;
-    }
-    // the parts must be the ranks 0..count-1 of one function, in order
-    const uint64_t *h0 = &hd[0];
-    const uint64_t n_total = h0[4], bucket = h0[8];
-    if (bucket < 1 || bucket > MPHF_MAX_BUCKET_SIZE || n_total >= (1ull << 32)) return MPHF_EINVAL;
-    const uint64_t nb = (n_total + bucket - 1) / bucket;
-    uint64_t keys = 0, nodes = 0, bits = 0, max_bucket = 0;
-    for (uint32_t s = 0; s < count; s++) {
-        const uint64_t *x = &hd[kShardHead * s];
-        uint64_t lo, hi;
-        shard_range(nb, s, count, &lo, &hi);
-        if (x[0] != kShardMagic || x[4] != n_total || x[7] != h0[7] || x[8] != bucket ||
-            x[9] != h0[9] || x[10] != h0[10] || x[3] != lo || x[2] != hi - lo || x[1] > n_total ||
-            x[5] > 4096ull * (hi - lo))
-            return MPHF_EINVAL;
-        // the part must hold its arrays (no sum below can wrap)
-        uint64_t room = lens[s] / 8 - kShardHead;
-        if (x[2] + 1 > room / 3) return MPHF_EINVAL;
-        room -= 3 * (x[2] + 1);
-        if (x[5] > room) return MPHF_EINVAL;
-        room -= x[5];
-        if (x[6] > 64 * room) return MPHF_EINVAL;
-        keys += x[1];
-        nodes += x[5];
-        bits += x[6];
-        max_bucket = x[11] > max_bucket ? x[11] : max_bucket;
-    }
-    if (keys != n_total) return MPHF_EINVAL;
-    mphf_t *h = new (std::nothrow) mphf;
-    if (!h) return MPHF_ENOMEM;
-    if (cudaGetDevice(&h->device) != cudaSuccess) {
-        cudaGetLastError();
-        delete h;
-        return MPHF_ECUDA;
-    }
-    if (allocator) {
-        h->alloc = *allocator;
-        h->has_alloc = true;
-    }
-    mphf_info &I = h->info;
-    I.n = n_total;
-    I.nb = nb;
-    I.leaf_size = (uint32_t)(h0[7] & 0xFFFF);
-    I.tree_shape = (uint32_t)(h0[7] >> 16);
-    I.bucket_size = (uint32_t)bucket;
-    I.key_bytes = (uint32_t)h0[9];
-    I.leaf_bijection = (uint32_t)h0[10];
-    I.n_nodes = nodes;
-    I.max_bucket = (uint32_t)max_bucket;
-    int rc = device_tables(h->device, I.leaf_size, I.leaf_bijection, I.tree_shape, &h->tabs);
-    if (rc != MPHF_OK) {
-        release(h, 0);
-        return rc;
-    }
-    Mem mem{allocator, st};
-    h->cum_keys = (uint64_t *)mem.get((nb + 1) * 8);
-    h->node_off = (uint64_t *)mem.get((nb + 1) * 8);
-    h->bit_pos = (uint64_t *)mem.get((nb + 1) * 8);
-    h->values = (uint64_t *)mem.get(nodes * 8);
-    uint64_t *tmp = (uint64_t *)mem.get((scan_tmp_words(nb + 2 > 4098 ? nb + 2 : 4098) + 64) * 8);
-    if (!h->cum_keys || !h->node_off || !h->bit_pos || !h->values || !tmp ||
-        alloc_packed(h, nb, n_total, bits, mem) != MPHF_OK) {
-        mem.put(tmp);
-        cudaStreamSynchronize(st);
-        release(h, st);
-        return MPHF_ENOMEM;
-    }
-    const uint64_t last[3] = {n_total, nodes, bits};  // the closing entry of each offset array
-    bool ok = cudaMemsetAsync(h->gr, 0, I.gr_words * 8 + 8, st) == cudaSuccess &&
-              cudaMemsetAsync(h->ef, 0, I.ef_words * 8 + 8, st) == cudaSuccess &&
-              cudaMemcpyAsync(h->cum_keys + nb, &last[0], 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(h->node_off + nb, &last[1], 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(h->bit_pos + nb, &last[2], 8, cudaMemcpyHostToDevice, st) == cudaSuccess;
-    uint64_t k0 = 0, n0 = 0, g0 = 0;
-    for (uint32_t s = 0; s < count && ok; s++) {
-        const uint64_t *x = &hd[kShardHead * s];
-        const uint64_t snb = x[2], b_lo = x[3], sn = x[5], sbits = x[6];
-        const uint64_t *w = (const uint64_t *)d_parts[s] + kShardHead;
-        const uint64_t *cum = w, *noff = cum + snb + 1, *bpos = noff + snb + 1, *vals = bpos + snb + 1;
-        const uint64_t *gr = vals + sn;
-        launch_shard_offsets(cum, snb, k0, h->cum_keys + b_lo, st);
-        launch_shard_offsets(noff, snb, n0, h->node_off + b_lo, st);
-        launch_shard_offsets(bpos, snb, g0, h->bit_pos + b_lo, st);
-        if (sn && cudaMemcpyAsync(h->values + n0, vals, sn * 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            ok = false;
-        launch_shard_bits(gr, sbits, g0, h->gr, st);
-        k0 += x[1];
-        n0 += sn;
-        g0 += sbits;
-    }
-    if (ok) write_ef_dirs(h, nb, tmp, st);
-    for (uint32_t s = 0; s < count; s++)
-        for (int k = 0; k < 4; k++) {
-            h->stats.trials[k] += hd[kShardHead * s + 16 + k];
-            h->stats.evals[k] += hd[kShardHead * s + 20 + k];
-        }
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) ok = false;
-    mem.put(tmp);
-    if (!ok) {
-        cudaGetLastError();
-        cudaStreamSynchronize(st);
-        release(h, st);
-        return MPHF_ECUDA;
-    }
-    *out = h;
-    return MPHF_OK;
 }
 
 static QueryView view_of(const mphf_t *h) {
@@ -1497,479 +1156,3 @@ int mphf_load(const void *h_buf, size_t len, const mphf_allocator *allocator, vo
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Build server with continuous batching.
-//
-// One serving search kernel (k_serve) stays on the device while there is
-// work and takes buckets from a ring in device memory.  A control thread:
-//   - admits queued requests in arrival order while a request slot and
-//     device memory are free: it runs their fingerprint, bucket sort and plan
-//     on the preparation stream (these kernels run beside the search, on the
-//     SM room the search leaves free) and stages their work items;
-//   - keeps the ring filled, a few items from each running request in turn,
-//     so a request admitted while others are on the device gets blocks
-//     within about one bucket's time;
-//   - polls the per-request bucket counters and packs (Golomb-Rice, Elias-
-//     Fano) each request as soon as its last bucket is done, while the others
-//     keep searching; the request completes on its own, not with a batch.
-// Every request goes through the same kernels as a plain build, so its
-// function is identical.
-namespace {
-
-struct ServerRequest {
-    uint64_t ticket = 0;
-    mphf_build_desc desc{};
-    mphf_request_times t{};
-    int status = MPHF_OK;
-    mphf_t *out = nullptr;
-    bool done = false;
-};
-
-double seconds_since(std::chrono::steady_clock::time_point t0) {
-    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-}
-
-// Device memory a build needs besides its keys: grouped lo words and bits,
-// node values and sizes, offsets, packed output (about 11 bytes per key).
-uint64_t build_bytes(const mphf_build_desc &d) {
-    uint64_t nb = d.bucket_size ? (d.n + d.bucket_size - 1) / d.bucket_size : 0;
-    return 16 * d.n + 48 * nb + (1u << 20);
-}
-
-constexpr uint32_t kRing = 1u << 16;           // work items the ring holds
-constexpr uint32_t kMaxSlots = MPHF_SERVER_MAX_REQUESTS;
-
-// A request on the device.
-struct Active {
-    ServerRequest *r = nullptr;
-    Job job;
-    uint32_t slot = 0;
-    WorkItem *staging = nullptr;  // its buckets' work items, largest first
-    uint64_t nb = 0, published = 0;
-    uint64_t reserve = 0;         // device bytes counted against the budget
-};
-
-}  // namespace
-
-struct mphf_server {
-    int device = 0;
-    mphf_server_cfg cfg{};
-    std::chrono::steady_clock::time_point t0;
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done;
-    std::deque<ServerRequest *> pending;
-    std::unordered_map<uint64_t, ServerRequest *> requests;
-    std::thread control;
-    uint64_t next_ticket = 1;
-    bool stop = false;
-    int fatal = MPHF_OK;  // a CUDA failure of the server itself
-    // device side
-    cudaStream_t prep = nullptr, search = nullptr, poll = nullptr;
-    ServeCtl *ctl = nullptr;
-    WorkItem *ring = nullptr;
-    InstDesc *insts = nullptr;
-    unsigned int *done = nullptr, *sm_count = nullptr;
-    uint64_t *pinned = nullptr;  // [0] new tail, [1] head seen, then done[] as 32-bit words
-    ServeLaunch launch{};
-};
-
-namespace {
-
-void finish(mphf_server_t *S, ServerRequest *r, int status, mphf_t *h) {
-    std::lock_guard<std::mutex> g(S->mu);
-    r->status = status;
-    r->out = status == MPHF_OK ? h : nullptr;
-    r->t.finished = seconds_since(S->t0);
-    r->done = true;
-    S->cv_done.notify_all();
-}
-
-// Fingerprints, sort, plan and work items of one request on the preparation
-// stream; its descriptor goes to slot a.slot.  Returns a server-wide error
-// (CUDA) or OK; a failure of the request alone is left in a.job.rc.
-int prepare(mphf_server_t *S, EngineCtx &c, Active &a) {
-    Job &j = a.job;
-    std::vector<Job *> jp{&j};
-    int rc = c.reserve(1, j.nb);
-    if (rc != MPHF_OK) return rc;
-    if ((rc = c.clear_order()) != MPHF_OK) return rc;
-    if ((rc = phase_plan(jp, c)) != MPHF_OK) return rc;
-    if (j.rc) return MPHF_OK;
-    if ((rc = phase_scatter(jp, c)) != MPHF_OK) return rc;
-    if (j.rc) return MPHF_OK;
-    a.nb = j.nb;
-    a.staging = (WorkItem *)c.mem.get(j.nb * sizeof(WorkItem) + 8);
-    if (!a.staging) {
-        fail_job(j, MPHF_ENOMEM, c.mem);
-        return MPHF_OK;
-    }
-    const cudaStream_t st = c.mem.st;
-    launch_exclusive_scan(c.size_hist, 4098, c.scan_tmp, st);
-    launch_items_by_size(j.h->cum_keys, j.nb, c.size_hist, c.size_cursor, a.staging, a.slot, st);
-    if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(S->insts + a.slot, &j.desc, sizeof(InstDesc), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess ||
-        cudaMemsetAsync(S->done + a.slot, 0, sizeof(unsigned int), st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        cudaGetLastError();
-        return MPHF_ECUDA;
-    }
-    return MPHF_OK;
-}
-
-// Sets the search's stop flag (copied from pinned memory, then synchronised).
-int set_stop(mphf_server_t *S, uint32_t v) {
-    uint32_t *p = (uint32_t *)S->pinned;
-    p[0] = v;
-    if (cudaMemcpyAsync(&S->ctl->stop, p, 4, cudaMemcpyHostToDevice, S->prep) != cudaSuccess ||
-        cudaStreamSynchronize(S->prep) != cudaSuccess) {
-        cudaGetLastError();
-        return MPHF_ECUDA;
-    }
-    return MPHF_OK;
-}
-
-void release_active(EngineCtx &c, Active &a) {
-    free_job_scratch(a.job, c.mem);
-    c.mem.put(a.staging);
-    a.staging = nullptr;
-}
-
-void server_control(mphf_server_t *S) {
-    cudaSetDevice(S->device);
-    EngineCtx c{Mem{nullptr, S->prep}};
-    std::vector<Active *> active;
-    std::vector<uint32_t> free_slots;
-    for (uint32_t i = S->cfg.max_requests; i-- > 0;) free_slots.push_back(i);
-    uint64_t tail = 0, head = 0;
-    bool running = false;  // a serving search was launched and may still run
-    size_t rr = 0;  // round-robin position over the active requests
-    const uint64_t low_water = 2ull * S->launch.working_blocks;
-    const unsigned long long idle_ns = (unsigned long long)S->cfg.idle_ms * 1000000ull;
-    auto fatal = [&](int rc) {
-        std::lock_guard<std::mutex> g(S->mu);
-        if (S->fatal == MPHF_OK) S->fatal = rc;
-    };
-    for (;;) {
-        bool progress = false;
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            if (S->fatal != MPHF_OK) {  // the device failed: every request gets the error
-                const int rc = S->fatal;
-                std::vector<ServerRequest *> left(S->pending.begin(), S->pending.end());
-                S->pending.clear();
-                lk.unlock();
-                for (ServerRequest *r : left) finish(S, r, rc, nullptr);
-                // the search may still read the active requests' arrays: stop it first
-                set_stop(S, 1);
-                cudaStreamSynchronize(S->search);
-                cudaGetLastError();
-                running = false;
-                for (Active *a : active) {
-                    if (a->job.h) fail_job(a->job, rc, c.mem);
-                    release_active(c, *a);
-                    finish(S, a->r, rc, nullptr);
-                    delete a;
-                }
-                active.clear();
-                break;
-            }
-        }
-        // 1. admission, in arrival order, while a slot and memory are free
-        for (;;) {
-            ServerRequest *r = nullptr;
-            {
-                std::unique_lock<std::mutex> lk(S->mu);
-                if (S->pending.empty() || free_slots.empty()) break;
-                size_t free_b = 0, total_b = 0;
-                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-                    cudaGetLastError();
-                    free_b = 0;
-                }
-                // memory of admitted requests is already allocated, so free_b counts it
-                const int64_t budget = (int64_t)free_b - (int64_t)S->cfg.hbm_reserve_bytes;
-                const uint64_t need = build_bytes(S->pending.front()->desc);
-                // a request that never fits still runs when nothing else is on the device
-                if ((int64_t)need > budget && !active.empty()) break;
-                r = S->pending.front();
-                S->pending.pop_front();
-                r->t.admitted = seconds_since(S->t0);
-            }
-            progress = true;
-            Active *a = new Active;
-            a->r = r;
-            a->slot = free_slots.back();
-            free_slots.pop_back();
-            mphf_build_params p;
-            mphf_default_params(&p);
-            p.leaf_size = r->desc.leaf_size;
-            p.bucket_size = r->desc.bucket_size;
-            p.key_bytes = r->desc.key_bytes;
-            p.leaf_bijection = r->desc.leaf_bijection;
-            p.tree_shape = r->desc.tree_shape;
-            p.max_value = r->desc.max_value ? r->desc.max_value : MPHF_DEFAULT_MAX_VALUE;
-            p.seeds_per_thread = r->desc.seeds_per_thread;
-            start_job(a->job, r->desc.d_keys, r->desc.n, p);
-            int rc = a->job.rc ? MPHF_OK : prepare(S, c, *a);
-            if (rc != MPHF_OK) fatal(rc);
-            if (rc != MPHF_OK || a->job.rc) {
-                const int st = rc != MPHF_OK ? rc : a->job.rc;
-                if (rc != MPHF_OK && a->job.h) fail_job(a->job, rc, c.mem);
-                release_active(c, *a);
-                free_slots.push_back(a->slot);
-                finish(S, r, st, nullptr);
-                delete a;
-                continue;
-            }
-            active.push_back(a);
-        }
-        // 2. keep the ring filled: a few items of each request in turn
-        if (!active.empty() && tail - head < low_water) {
-            const uint64_t start = tail;
-            bool any = true;
-            while (tail - head < low_water + 64 && any) {
-                any = false;
-                for (size_t k = 0; k < active.size() && tail - head < low_water + 64; k++) {
-                    Active &a = *active[(rr + k) % active.size()];
-                    if (a.published >= a.nb) continue;
-                    uint64_t take = a.nb - a.published;
-                    take = take > 8 ? 8 : take;
-                    take = take > kRing - (tail % kRing) ? kRing - (tail % kRing) : take;  // no wrap
-                    if (cudaMemcpyAsync(S->ring + tail % kRing, a.staging + a.published,
-                                        take * sizeof(WorkItem), cudaMemcpyDeviceToDevice,
-                                        S->prep) != cudaSuccess)
-                        fatal(MPHF_ECUDA);
-                    a.published += take;
-                    tail += take;
-                    any = true;
-                }
-                rr++;
-            }
-            if (tail != start) {
-                S->pinned[0] = tail;
-                if (cudaMemcpyAsync(&S->ctl->tail, S->pinned, 8, cudaMemcpyHostToDevice, S->prep) !=
-                        cudaSuccess ||
-                    cudaStreamSynchronize(S->prep) != cudaSuccess) {
-                    cudaGetLastError();
-                    fatal(MPHF_ECUDA);
-                }
-                progress = true;
-            }
-        }
-        // 3. the search must be on the device while items wait (its blocks
-        // leave only when told to, or after the idle bound)
-        if (tail > head) {
-            if (running) {
-                const cudaError_t q = cudaStreamQuery(S->search);
-                if (q != cudaSuccess && q != cudaErrorNotReady) fatal(MPHF_ECUDA);
-                cudaGetLastError();  // a search still running is not an error
-                running = q != cudaSuccess;
-            }
-            if (!running) {
-                if (cudaMemsetAsync(S->sm_count, 0, kServeMaxSms * 4, S->search) != cudaSuccess)
-                    fatal(MPHF_ECUDA);
-                launch_serve(S->insts, S->ring, kRing, S->ctl, S->done, S->sm_count,
-                             S->cfg.reserved_sms, idle_ns, S->launch, S->search);
-                if (cudaGetLastError() != cudaSuccess) fatal(MPHF_ECUDA);
-                running = true;
-            }
-        }
-        // 4. poll the queue head and the per-request bucket counters
-        if (!active.empty()) {
-            uint32_t *d32 = (uint32_t *)(S->pinned + 2);
-            if (cudaMemcpyAsync(S->pinned + 1, &S->ctl->head, 8, cudaMemcpyDeviceToHost, S->poll) != cudaSuccess ||
-                cudaMemcpyAsync(d32, S->done, S->cfg.max_requests * 4, cudaMemcpyDeviceToHost, S->poll) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(S->poll) != cudaSuccess) {
-                cudaGetLastError();
-                fatal(MPHF_ECUDA);
-            }
-            head = S->pinned[1] < tail ? S->pinned[1] : tail;
-            // 5. pack every request whose buckets are all done
-            for (size_t k = 0; k < active.size();) {
-                Active &a = *active[k];
-                if (a.published < a.nb || d32[a.slot] < a.nb) {
-                    k++;
-                    continue;
-                }
-                std::vector<Job *> jp{&a.job};
-                int rc = phase_pack(jp, c);
-                if (rc != MPHF_OK) fatal(rc);
-                const int st = rc != MPHF_OK ? rc : a.job.rc;
-                mphf_t *h = a.job.h;
-                release_active(c, a);
-                if (st != MPHF_OK && h) {
-                    if (!a.job.rc) fail_job(a.job, st, c.mem);
-                    h = nullptr;
-                }
-                free_slots.push_back(a.slot);
-                finish(S, a.r, st, h);
-                delete active[k];
-                active.erase(active.begin() + (long)k);
-                progress = true;
-            }
-        }
-        // 6. nothing on the device: the search leaves, so that the next
-        // request's preparation has the whole GPU
-        if (running && active.empty()) {
-            bool idle;
-            {
-                std::lock_guard<std::mutex> g(S->mu);
-                idle = S->pending.empty();
-            }
-            if (idle) {
-                if (set_stop(S, 1) != MPHF_OK || cudaStreamSynchronize(S->search) != cudaSuccess ||
-                    set_stop(S, 0) != MPHF_OK) {
-                    cudaGetLastError();
-                    fatal(MPHF_ECUDA);
-                }
-                running = false;
-                head = tail;  // every published item was claimed and done
-            }
-        }
-        {
-            std::unique_lock<std::mutex> lk(S->mu);
-            if (S->stop && S->pending.empty() && active.empty()) break;
-            if (!progress) {
-                if (active.empty())
-                    S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
-                else
-                    S->cv_work.wait_for(lk, std::chrono::microseconds(300));
-            }
-        }
-    }
-    // no work left: the search's blocks leave, then the server's arrays can go
-    set_stop(S, 1);
-    cudaStreamSynchronize(S->search);
-    cudaGetLastError();
-    c.release();
-}
-
-}  // namespace
-
-extern "C" {
-
-int mphf_server_create(const mphf_server_cfg *cfg, mphf_server_t **out) {
-    if (!out) return MPHF_EINVAL;
-    *out = nullptr;
-    mphf_server_t *S = new (std::nothrow) mphf_server;
-    if (!S) return MPHF_ENOMEM;
-    S->cfg.max_requests = cfg && cfg->max_requests ? cfg->max_requests : 64;
-    S->cfg.reserved_sms = cfg ? cfg->reserved_sms : 4;
-    S->cfg.hbm_reserve_bytes = cfg && cfg->hbm_reserve_bytes ? cfg->hbm_reserve_bytes : (1ull << 30);
-    S->cfg.idle_ms = cfg && cfg->idle_ms ? cfg->idle_ms : 10000;
-    S->cfg.threads = cfg && cfg->threads ? cfg->threads : 512;
-    if (S->cfg.max_requests > kMaxSlots || S->cfg.idle_ms > 600000 || S->cfg.threads % 32 ||
-        S->cfg.threads < 64 || S->cfg.threads > 512) {
-        delete S;
-        return MPHF_EINVAL;
-    }
-    S->t0 = std::chrono::steady_clock::now();
-    int lo_prio = 0, hi_prio = 0;
-    bool ok = cudaGetDevice(&S->device) == cudaSuccess &&
-              cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&S->prep, cudaStreamNonBlocking, hi_prio) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&S->search, cudaStreamNonBlocking, lo_prio) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&S->poll, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc(&S->ctl, sizeof(ServeCtl)) == cudaSuccess &&
-              cudaMalloc(&S->ring, kRing * sizeof(WorkItem)) == cudaSuccess &&
-              cudaMalloc(&S->insts, kMaxSlots * sizeof(InstDesc)) == cudaSuccess &&
-              cudaMalloc(&S->done, kMaxSlots * sizeof(unsigned int)) == cudaSuccess &&
-              cudaMalloc(&S->sm_count, kServeMaxSms * sizeof(unsigned int)) == cudaSuccess &&
-              cudaMallocHost(&S->pinned, 8 * (2 + kMaxSlots / 2)) == cudaSuccess &&
-              cudaMemset(S->ctl, 0, sizeof(ServeCtl)) == cudaSuccess &&
-              cudaMemset(S->done, 0, kMaxSlots * sizeof(unsigned int)) == cudaSuccess &&
-              cudaDeviceSynchronize() == cudaSuccess;
-    if (ok) S->launch = plan_serve_launch(S->cfg.threads, S->cfg.reserved_sms);
-    if (ok) {
-        try {
-            S->control = std::thread(server_control, S);
-        } catch (...) {
-            ok = false;
-        }
-    }
-    if (!ok) {
-        cudaGetLastError();
-        cudaFree(S->ctl);
-        cudaFree(S->ring);
-        cudaFree(S->insts);
-        cudaFree(S->done);
-        cudaFree(S->sm_count);
-        if (S->pinned) cudaFreeHost(S->pinned);
-        for (cudaStream_t st : {S->prep, S->search, S->poll})
-            if (st) cudaStreamDestroy(st);
-        delete S;
-        return MPHF_ECUDA;
-    }
-    *out = S;
-    return MPHF_OK;
-}
-
-int mphf_server_submit(mphf_server_t *S, const mphf_build_desc *desc, uint64_t *ticket) {
-    if (!S || !desc || !ticket) return MPHF_EINVAL;
-    ServerRequest *r = new (std::nothrow) ServerRequest;
-    if (!r) return MPHF_ENOMEM;
-    r->desc = *desc;
-    std::lock_guard<std::mutex> g(S->mu);
-    if (S->stop || S->fatal != MPHF_OK) {
-        delete r;
-        return S->fatal != MPHF_OK ? S->fatal : MPHF_EBUSY;
-    }
-    r->ticket = S->next_ticket++;
-    r->t.submitted = seconds_since(S->t0);
-    try {
-        S->requests[r->ticket] = r;
-        S->pending.push_back(r);
-    } catch (...) {
-        S->requests.erase(r->ticket);
-        delete r;
-        return MPHF_ENOMEM;
-    }
-    *ticket = r->ticket;
-    S->cv_work.notify_one();
-    return MPHF_OK;
-}
-
-int mphf_server_poll(mphf_server_t *S, uint64_t ticket, uint32_t timeout_ms, mphf_t **out,
-                     int *status, mphf_request_times *times) {
-    if (!S || !out || !status) return MPHF_EINVAL;
-    *out = nullptr;
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->requests.find(ticket);
-    if (it == S->requests.end()) return MPHF_EINVAL;
-    ServerRequest *r = it->second;
-    if (!r->done)
-        S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; });
-    if (!r->done) return MPHF_ETIMEOUT;
-    *out = r->out;
-    *status = r->status;
-    if (times) *times = r->t;
-    S->requests.erase(it);
-    delete r;
-    return MPHF_OK;
-}
-
-int mphf_server_destroy(mphf_server_t *S) {
-    if (!S) return MPHF_EINVAL;
-    {
-        std::lock_guard<std::mutex> g(S->mu);
-        S->stop = true;
-        S->cv_work.notify_all();
-    }
-    if (S->control.joinable()) S->control.join();
-    cudaFree(S->ctl);
-    cudaFree(S->ring);
-    cudaFree(S->insts);
-    cudaFree(S->done);
-    cudaFree(S->sm_count);
-    cudaFreeHost(S->pinned);
-    for (cudaStream_t st : {S->prep, S->search, S->poll}) cudaStreamDestroy(st);
-    for (auto &kv : S->requests) {
-        if (kv.second->out) mphf_free(kv.second->out);
-        delete kv.second;
-    }
-    delete S;
-    return MPHF_OK;
-}
-
-}  // extern "C"
