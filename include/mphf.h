@@ -223,6 +223,44 @@ int mphf_build_enqueue(mphf_t *h, const void *d_keys, void *stream);
  * the next successful enqueue and finish. */
 int mphf_build_finish(mphf_t *h, void *stream);
 
+/* Prepared builds searched together: the buckets of all of them go through
+ * ONE persistent search launch (the work order of mphf_build_batch), and the
+ * whole batch is enqueued without allocation or host synchronisation, so
+ * that it, too, can be captured in a CUDA graph.  The batch refers to the
+ * handles (it does not own them): they must stay allocated while the batch
+ * is used, and no handle may be enqueued elsewhere while the batch's work on
+ * it is in flight. */
+typedef struct mphf_batch mphf_batch_t;
+
+/* Makes a batch of count >= 1 distinct handles from mphf_build_prepare, all
+ * on the current device.  threads_per_block (0 = 512 when some build has
+ * RecSplit lower levels of leaf size >= 14, else 256; otherwise a multiple of
+ * 32 in [64, 512]) and blocks_per_sm (0 = the occupancy limit) shape the
+ * search launch.  The batch's own scratch comes from allocator (NULL =
+ * stream-ordered cudaMallocAsync).  Errors: MPHF_EINVAL (a NULL, repeated,
+ * unprepared or other-device handle, a bad launch shape, 2^32 or more buckets
+ * in all), MPHF_ENOMEM, MPHF_ECUDA.  Synchronises the device. */
+int mphf_batch_prepare(mphf_t *const *handles, uint32_t count, uint32_t threads_per_block,
+                       uint32_t blocks_per_sm, const mphf_allocator *allocator,
+                       mphf_batch_t **out);
+
+/* Issues every build of the batch on the stream: handle i builds from the
+ * keys at d_keys[i] (a host array of count device pointers, each 8-byte
+ * aligned, holding that handle's n keys; the pointers are read now, the keys
+ * when the work runs).  Memsets and kernels only.  MPHF_EINVAL for a bad
+ * pointer or another device current than the batch's. */
+int mphf_batch_enqueue(mphf_batch_t *b, const void *const *d_keys, void *stream);
+
+/* Waits for the stream, reads all builds' totals back in one copy and
+ * finishes each handle as mphf_build_finish would.  statuses (may be NULL)
+ * receives each build's code; the return value is MPHF_OK if all succeeded,
+ * else the first failure (the failed handles stay unusable). */
+int mphf_batch_finish(mphf_batch_t *b, void *stream, int *statuses);
+
+/* Releases the batch's scratch (not its handles).  Synchronises its device.
+ * MPHF_EINVAL for NULL. */
+int mphf_batch_free(mphf_batch_t *b);
+
 /* ---------------------------------------------------------------------------
  * One function built on several GPUs (Section 5.2, "Multi-Threading": each
  * worker builds a consecutive range of buckets; the local Golomb-Rice

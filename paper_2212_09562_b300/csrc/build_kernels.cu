@@ -1809,7 +1809,12 @@ SearchLaunch plan_search_launch(uint32_t max_m, uint32_t items, uint32_t threads
     int dev = 0, sms = 148, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem_bytes);
+    // the limit is the kernel's, not this launch's: it stays at the largest
+    // bucket any launch may hold, so that a smaller launch planned later does
+    // not refuse a larger one planned earlier (a prepared build, a captured graph)
+    const uint32_t limit = search_smem(MPHF_MAX_BUCKET);
+    cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(L.smem_bytes > limit ? L.smem_bytes : limit));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_search, L.threads, L.smem_bytes);
     if (occ < 1) occ = 1;
     uint32_t per_sm = blocks_per_sm ? (blocks_per_sm < (uint32_t)occ ? blocks_per_sm : occ) : occ;
@@ -2078,6 +2083,31 @@ __global__ void k_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel
 void launch_select_dir(uint64_t nwords, const uint64_t *dir, uint64_t *sel, cudaStream_t st) {
     if (nwords == 0) return;
     k_select_dir<<<grid_for(nwords, 256), 256, 0, st>>>(nwords, dir, sel);
+    note_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// The totals of a batch of prepared builds in one array, so that one copy to
+// the host finishes them all: per build 16 words, [0] its status word (status
+// bits, largest bucket above bit 32), [1] stored nodes, [2] code bits, [8..15]
+// its search counters; the other words are zero.
+__global__ void k_gather_totals(const BuildTotalsSrc *src, uint32_t count, uint64_t *out) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < 16ull * count;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const BuildTotalsSrc &s = src[t >> 4];
+        const uint32_t j = (uint32_t)(t & 15);
+        uint64_t v = 0;
+        if (j == 0) v = ((uint64_t)s.status[1] << 32) | s.status[0];
+        else if (j == 1) v = *s.nodes;
+        else if (j == 2) v = *s.bits;
+        else if (j >= 8) v = s.counters[j - 8];
+        out[t] = v;
+    }
+}
+
+void launch_gather_totals(const BuildTotalsSrc *src, uint32_t count, uint64_t *out, cudaStream_t st) {
+    if (count == 0) return;
+    k_gather_totals<<<grid_for(16ull * count, 256), 256, 0, st>>>(src, count, out);
     note_launches(1);
 }
 

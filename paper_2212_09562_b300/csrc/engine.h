@@ -172,6 +172,17 @@ void launch_ef_planned(const uint64_t *cum_keys, const uint64_t *bit_pos, uint64
                        EfPlan *p, uint64_t *ef, uint64_t max_high1, uint64_t *rank1, uint64_t *tmp,
                        cudaStream_t st);
 
+// Where a prepared build keeps its totals on the device (status word, stored
+// nodes, code bits, search counters); k_gather_totals packs them 16 words per
+// build.
+struct BuildTotalsSrc {
+    const uint32_t *status;  // [0] status bits, [1] largest bucket
+    const uint64_t *nodes;
+    const uint64_t *bits;
+    const uint64_t *counters;  // 8 words
+};
+void launch_gather_totals(const BuildTotalsSrc *src, uint32_t count, uint64_t *out, cudaStream_t st);
+
 // Building one function on several GPUs (bucket ranges, Section 5.2).
 // Keys grouped by the rank owning their bucket (nb buckets, `world` ranges):
 // counts[r] += keys of rank r; then each key to cursor[r]++ in `out`.

@@ -17,7 +17,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "handle.h"
 
@@ -52,9 +54,170 @@ void release_plan(mphf_t *h, Mem &mem) {
     h->plan = nullptr;
 }
 
+namespace {
+
+bool on_device(int want) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return dev == want;
+}
+
+// The scratch that one search launch shares over all of its builds: the
+// bucket-size histogram and cursors of the work order, the queue head, the
+// steal queue.
+int zero_shared(uint64_t *size_hist, uint32_t *size_cursor, uint32_t *head, StealQueue *steal,
+                cudaStream_t st) {
+    if (cudaMemsetAsync(size_hist, 0, 4098 * 8, st) != cudaSuccess ||
+        cudaMemsetAsync(size_cursor, 0, 4097 * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(head, 0, 64, st) != cudaSuccess ||
+        cudaMemsetAsync(steal, 0, kStealBytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
+    }
+    return MPHF_OK;
+}
+
+// A build's own outputs and scratch, cleared before it is enqueued again.
+int zero_build(mphf_t *h, cudaStream_t st) {
+    BuildPlan &b = *h->plan;
+    const uint64_t n = b.n, k = b.nb + 1;
+    const EfDims e0 = ef_dims(k, n);
+    h->ready = false;
+    struct Zero {
+        void *p;
+        size_t bytes;
+    } zeros[] = {{h->cum_keys, k * 8},
+                 {h->node_off, k * 8},
+                 {h->bit_pos, k * 8},
+                 {b.cursor, k * 4},
+                 {b.small, 64},
+                 {b.counters, 64},
+                 {h->gr, (b.cap_bits / 64 + 2) * 8},
+                 {h->ef, (e0.low_words + e0.high_words + b.max_low1 + b.max_high1 + 1) * 8},
+                 {h->ef_dir, (h->ef_dir_len[0] + h->ef_dir_len[1] + 2 * h->ef_sel_len) * 8}};
+    for (const Zero &z : zeros)
+        if (cudaMemsetAsync(z.p, 0, z.bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            return MPHF_ECUDA;
+        }
+    return MPHF_OK;
+}
+
+// a1-a3 of one build: fingerprints, bucket sizes (counted into size_hist,
+// which may be shared with other builds of the same search launch), plan,
+// offsets, and its keys grouped by bucket.
+void enqueue_front(mphf_t *h, const void *d_keys, uint64_t *size_hist, cudaStream_t st) {
+    BuildPlan &b = *h->plan;
+    const uint64_t n = b.n, nb = b.nb, k = nb + 1;
+    const uint32_t kb = b.p.key_bytes;
+    const BucketRange R{nb, 0};
+    if (b.sort_g)
+        launch_fp_hist_blk(d_keys, n, kb, nb, R, b.sort_g, h->cum_keys, b.blk, b.small, st);
+    else
+        launch_fp_hist(d_keys, n, kb, nb, R, h->cum_keys, b.small, st);
+    launch_plan(h->cum_keys, nb, h->tabs.nodes, h->node_off, b.small, b.small + 1, size_hist, st);
+    launch_exclusive_scan(h->cum_keys, k, b.scan_tmp, st);
+    launch_exclusive_scan(h->node_off, k, b.scan_tmp, st);
+    if (b.sort_g)
+        launch_scatter_blk(d_keys, n, kb, nb, R, b.sort_g, h->cum_keys, b.blk, b.lo_s, b.bb_s, b.small, st);
+    else
+        launch_scatter(d_keys, n, kb, nb, R, h->cum_keys, b.cursor, b.lo_s, b.bb_s, b.small, st);
+}
+
+// a8 of one searched build: Golomb-Rice lengths and bits, Elias-Fano from the
+// device totals, query directories, search counters.
+void enqueue_back(mphf_t *h, cudaStream_t st) {
+    BuildPlan &b = *h->plan;
+    const uint64_t n = b.n, nb = b.nb, k = nb + 1;
+    const uint32_t leaf = b.p.leaf_size, bij = b.p.leaf_bijection;
+    const EfDims e0 = ef_dims(k, n);
+    launch_gr_lengths(h->values, b.node_m, h->node_off, nb, h->tabs.tau, leaf, bij, h->bit_pos, st);
+    launch_exclusive_scan(h->bit_pos, k, b.scan_tmp, st);
+    launch_gr_write(h->values, b.node_m, h->node_off, h->bit_pos, nb, h->tabs.tau, h->tabs.fixed,
+                    h->cum_keys, leaf, bij, h->gr, st, b.cap_bits, b.small);
+    uint64_t *rank0 = h->ef_dir, *rank1 = rank0 + h->ef_dir_len[0];
+    uint64_t *sel0 = rank1 + h->ef_dir_len[1], *sel1 = sel0 + h->ef_sel_len;
+    launch_ef_planned(h->cum_keys, h->bit_pos, nb, b.cap_bits, b.efp, h->ef, b.max_high1, rank1,
+                      b.scan_tmp, st);
+    launch_rank_dir(h->ef + e0.low_words, e0.high_words, rank0, b.scan_tmp, st);
+    launch_select_dir(e0.high_words, rank0, sel0, st);
+    launch_select_dir(b.max_high1, rank1, sel1, st);
+    launch_stats(h->values, b.node_m, n, leaf, bij, b.p.tree_shape, b.counters, st, h->node_off + nb);
+}
+
+// Makes h a usable function from its totals read back to the host: w[0] the
+// status word, w[1] stored nodes, w[2] code bits, w[8..15] search counters.
+int finish_from(mphf_t *h, const uint64_t *w) {
+    BuildPlan &b = *h->plan;
+    const uint64_t nb = b.nb;
+    const uint32_t status = (uint32_t)w[0];
+    if (status) return status_code(status);
+    mphf_info &I = h->info;
+    I.max_bucket = (uint32_t)(w[0] >> 32);
+    I.n_nodes = w[1];
+    I.gr_bits = w[2];
+    I.gr_words = (I.gr_bits + 63) / 64;
+    const EfDims e0 = ef_dims(nb + 1, b.n), e1 = ef_dims(nb + 1, I.gr_bits);
+    I.ef_low_bits[0] = e0.L;
+    I.ef_low_bits[1] = e1.L;
+    I.ef_seq_words[0] = e0.low_words;
+    I.ef_seq_words[1] = e0.high_words;
+    I.ef_seq_words[2] = e1.low_words;
+    I.ef_seq_words[3] = e1.high_words;
+    I.ef_words = e0.low_words + e0.high_words + e1.low_words + e1.high_words;
+    for (int k = 0; k < 4; k++) {
+        h->stats.trials[k] = w[8 + k];
+        h->stats.evals[k] = w[12 + k];
+    }
+    h->ready = true;
+    return MPHF_OK;
+}
+
+}  // namespace
+
 }  // namespace rs
 
 using namespace rs;
+
+// A batch of prepared builds searched by one persistent launch: the work
+// order over all of their buckets, the launch's shared scratch, and one array
+// of every build's totals.
+struct mphf_batch {
+    int device = 0;
+    std::vector<mphf_t *> hs;
+    uint64_t slots = 0;  // buckets of all builds
+    mphf_allocator alloc{};
+    bool has_alloc = false;
+    SearchLaunch L{};
+    uint64_t *size_hist = nullptr, *scan_tmp = nullptr, *totals = nullptr;
+    uint32_t *size_cursor = nullptr, *head = nullptr;
+    WorkItem *items = nullptr;
+    InstDesc *d_inst = nullptr;
+    StealQueue *steal = nullptr;
+    BuildTotalsSrc *src = nullptr;
+    uint64_t *host = nullptr;  // pinned: 16 words per build
+};
+
+namespace {
+
+void release_batch(mphf_batch *b) {
+    if (!b) return;
+    Mem mem{b->has_alloc ? &b->alloc : nullptr, 0};
+    void *ptrs[] = {b->size_hist, b->scan_tmp, b->totals, b->size_cursor, b->head,
+                    b->items, b->d_inst, b->steal, b->src};
+    cudaDeviceSynchronize();
+    for (void *p : ptrs) mem.put(p);
+    cudaStreamSynchronize(0);
+    if (b->host) cudaFreeHost(b->host);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // namespace
+
 
 extern "C" {
 
@@ -200,69 +363,17 @@ int mphf_build_prepare(uint64_t n, const mphf_build_params *p, uint64_t gr_capac
 
 int mphf_build_enqueue(mphf_t *h, const void *d_keys, void *stream) {
     if (!h || !h->plan || !d_keys || ((uintptr_t)d_keys & 7)) return MPHF_EINVAL;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        return MPHF_ECUDA;
-    }
-    if (dev != h->device) return MPHF_EINVAL;
+    if (!on_device(h->device)) return MPHF_EINVAL;
     BuildPlan &b = *h->plan;
     const cudaStream_t st = (cudaStream_t)stream;
-    const uint64_t n = b.n, nb = b.nb, k = nb + 1;
-    const uint32_t kb = b.p.key_bytes, leaf = b.p.leaf_size, bij = b.p.leaf_bijection;
-    const BucketRange R{nb, 0};
-    h->ready = false;
-    const EfDims e0 = ef_dims(k, n);
-    struct Zero {
-        void *p;
-        size_t bytes;
-    } zeros[] = {{h->cum_keys, k * 8},
-                 {h->node_off, k * 8},
-                 {h->bit_pos, k * 8},
-                 {b.cursor, k * 4},
-                 {b.small, 64},
-                 {b.counters, 64},
-                 {b.size_hist, 4098 * 8},
-                 {b.size_cursor, 4097 * 4},
-                 {b.head, 64},
-                 {b.steal, kStealBytes},
-                 {h->gr, (b.cap_bits / 64 + 2) * 8},
-                 {h->ef, (e0.low_words + e0.high_words + b.max_low1 + b.max_high1 + 1) * 8},
-                 {h->ef_dir, (h->ef_dir_len[0] + h->ef_dir_len[1] + 2 * h->ef_sel_len) * 8}};
-    for (const Zero &z : zeros)
-        if (cudaMemsetAsync(z.p, 0, z.bytes, st) != cudaSuccess) {
-            cudaGetLastError();
-            return MPHF_ECUDA;
-        }
-    // a1-a3: fingerprints, bucket sizes, plan, offsets
-    if (b.sort_g)
-        launch_fp_hist_blk(d_keys, n, kb, nb, R, b.sort_g, h->cum_keys, b.blk, b.small, st);
-    else
-        launch_fp_hist(d_keys, n, kb, nb, R, h->cum_keys, b.small, st);
-    launch_plan(h->cum_keys, nb, h->tabs.nodes, h->node_off, b.small, b.small + 1, b.size_hist, st);
-    launch_exclusive_scan(h->cum_keys, k, b.scan_tmp, st);
-    launch_exclusive_scan(h->node_off, k, b.scan_tmp, st);
-    // keys by bucket, the work order, a4-a7: the searches
-    if (b.sort_g)
-        launch_scatter_blk(d_keys, n, kb, nb, R, b.sort_g, h->cum_keys, b.blk, b.lo_s, b.bb_s, b.small, st);
-    else
-        launch_scatter(d_keys, n, kb, nb, R, h->cum_keys, b.cursor, b.lo_s, b.bb_s, b.small, st);
+    if (zero_shared(b.size_hist, b.size_cursor, b.head, b.steal, st) != MPHF_OK ||
+        zero_build(h, st) != MPHF_OK)
+        return MPHF_ECUDA;
+    enqueue_front(h, d_keys, b.size_hist, st);
     launch_exclusive_scan(b.size_hist, 4098, b.scan_tmp, st);
-    launch_items_by_size(h->cum_keys, nb, b.size_hist, b.size_cursor, b.items, 0, st);
-    launch_search(b.d_inst, 1, b.items, (uint32_t)nb, b.head, b.L, b.steal, st);
-    // a8: Golomb-Rice lengths and bits, Elias-Fano from the device totals
-    launch_gr_lengths(h->values, b.node_m, h->node_off, nb, h->tabs.tau, leaf, bij, h->bit_pos, st);
-    launch_exclusive_scan(h->bit_pos, k, b.scan_tmp, st);
-    launch_gr_write(h->values, b.node_m, h->node_off, h->bit_pos, nb, h->tabs.tau, h->tabs.fixed,
-                    h->cum_keys, leaf, bij, h->gr, st, b.cap_bits, b.small);
-    uint64_t *rank0 = h->ef_dir, *rank1 = rank0 + h->ef_dir_len[0];
-    uint64_t *sel0 = rank1 + h->ef_dir_len[1], *sel1 = sel0 + h->ef_sel_len;
-    launch_ef_planned(h->cum_keys, h->bit_pos, nb, b.cap_bits, b.efp, h->ef, b.max_high1, rank1,
-                      b.scan_tmp, st);
-    launch_rank_dir(h->ef + e0.low_words, e0.high_words, rank0, b.scan_tmp, st);
-    launch_select_dir(e0.high_words, rank0, sel0, st);
-    launch_select_dir(b.max_high1, rank1, sel1, st);
-    launch_stats(h->values, b.node_m, n, leaf, bij, b.p.tree_shape, b.counters, st, h->node_off + nb);
+    launch_items_by_size(h->cum_keys, b.nb, b.size_hist, b.size_cursor, b.items, 0, st);
+    launch_search(b.d_inst, 1, b.items, (uint32_t)b.nb, b.head, b.L, b.steal, st);
+    enqueue_back(h, st);
     return cudaGetLastError() == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
 }
 
@@ -270,35 +381,153 @@ int mphf_build_finish(mphf_t *h, void *stream) {
     if (!h || !h->plan) return MPHF_EINVAL;
     BuildPlan &b = *h->plan;
     const cudaStream_t st = (cudaStream_t)stream;
-    const uint64_t nb = b.nb;
     if (cudaMemcpyAsync(b.host, b.small, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(b.host + 1, h->node_off + nb, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(b.host + 2, h->bit_pos + nb, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(b.host + 1, h->node_off + b.nb, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(b.host + 2, h->bit_pos + b.nb, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(b.host + 8, b.counters, 64, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return MPHF_ECUDA;
     }
-    const uint32_t status = (uint32_t)b.host[0];
-    if (status) return status_code(status);
-    mphf_info &I = h->info;
-    I.max_bucket = (uint32_t)(b.host[0] >> 32);
-    I.n_nodes = b.host[1];
-    I.gr_bits = b.host[2];
-    I.gr_words = (I.gr_bits + 63) / 64;
-    const EfDims e0 = ef_dims(nb + 1, b.n), e1 = ef_dims(nb + 1, I.gr_bits);
-    I.ef_low_bits[0] = e0.L;
-    I.ef_low_bits[1] = e1.L;
-    I.ef_seq_words[0] = e0.low_words;
-    I.ef_seq_words[1] = e0.high_words;
-    I.ef_seq_words[2] = e1.low_words;
-    I.ef_seq_words[3] = e1.high_words;
-    I.ef_words = e0.low_words + e0.high_words + e1.low_words + e1.high_words;
-    for (int k = 0; k < 4; k++) {
-        h->stats.trials[k] = b.host[8 + k];
-        h->stats.evals[k] = b.host[12 + k];
+    return finish_from(h, b.host);
+}
+
+int mphf_batch_prepare(mphf_t *const *handles, uint32_t count, uint32_t threads_per_block,
+                       uint32_t blocks_per_sm, const mphf_allocator *allocator, mphf_batch_t **out) {
+    if (!out) return MPHF_EINVAL;
+    *out = nullptr;
+    if (!handles || count == 0 ||
+        (threads_per_block &&
+         (threads_per_block % 32 || threads_per_block > 512 || threads_per_block < 64)))
+        return MPHF_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
     }
-    h->ready = true;
+    std::vector<mphf_t *> hs(handles, handles + count), sorted(hs);
+    uint64_t slots = 0;
+    bool wide = false;
+    for (mphf_t *h : hs) {
+        if (!h || !h->plan || h->device != dev) return MPHF_EINVAL;
+        slots += h->plan->nb;
+        wide |= h->plan->p.tree_shape == MPHF_TREE_RECSPLIT && h->plan->p.leaf_size >= 14;
+    }
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return MPHF_EINVAL;
+    if (slots > 0xFFFFFFFFull) return MPHF_EINVAL;
+    mphf_batch *b = new (std::nothrow) mphf_batch;
+    if (!b) return MPHF_ENOMEM;
+    b->device = dev;
+    b->hs = hs;
+    b->slots = slots;
+    if (allocator) {
+        b->alloc = *allocator;
+        b->has_alloc = true;
+    }
+    Mem mem{b->has_alloc ? &b->alloc : nullptr, 0};
+    b->size_hist = (uint64_t *)mem.get(4098 * 8);
+    b->scan_tmp = (uint64_t *)mem.get((scan_tmp_words(4098) + 64) * 8);
+    b->totals = (uint64_t *)mem.get(16ull * count * 8);
+    b->size_cursor = (uint32_t *)mem.get(4097 * 4);
+    b->head = (uint32_t *)mem.get(64);
+    b->items = (WorkItem *)mem.get(slots * sizeof(WorkItem));
+    b->d_inst = (InstDesc *)mem.get(count * sizeof(InstDesc));
+    b->steal = (StealQueue *)mem.get(kStealBytes);
+    b->src = (BuildTotalsSrc *)mem.get(count * sizeof(BuildTotalsSrc));
+    if (!b->size_hist || !b->scan_tmp || !b->totals || !b->size_cursor || !b->head || !b->items ||
+        !b->d_inst || !b->steal || !b->src) {
+        release_batch(b);
+        return MPHF_ENOMEM;
+    }
+    if (cudaMallocHost(&b->host, 16ull * count * 8) != cudaSuccess) {
+        cudaGetLastError();
+        b->host = nullptr;
+        release_batch(b);
+        return MPHF_ECUDA;
+    }
+    // every build's search descriptor (fixed since its prepare) and the
+    // places of its totals, in batch order
+    std::vector<BuildTotalsSrc> src(count);
+    bool ok = true;
+    for (uint32_t i = 0; i < count && ok; i++) {
+        mphf_t *h = hs[i];
+        BuildPlan &p = *h->plan;
+        src[i] = BuildTotalsSrc{p.small, h->node_off + p.nb, h->bit_pos + p.nb, p.counters};
+        ok = cudaMemcpyAsync(b->d_inst + i, p.d_inst, sizeof(InstDesc), cudaMemcpyDeviceToDevice,
+                             0) == cudaSuccess;
+    }
+    ok = ok && cudaMemcpyAsync(b->src, src.data(), count * sizeof(BuildTotalsSrc),
+                               cudaMemcpyHostToDevice, 0) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release_batch(b);
+        return MPHF_ECUDA;
+    }
+    b->L = plan_search_launch(MPHF_MAX_BUCKET, (uint32_t)slots,
+                              threads_per_block ? threads_per_block : (wide ? 512u : 256u),
+                              blocks_per_sm);
+    *out = b;
+    return MPHF_OK;
+}
+
+int mphf_batch_enqueue(mphf_batch_t *b, const void *const *d_keys, void *stream) {
+    if (!b || !d_keys) return MPHF_EINVAL;
+    const uint32_t count = (uint32_t)b->hs.size();
+    for (uint32_t i = 0; i < count; i++)
+        if (!d_keys[i] || ((uintptr_t)d_keys[i] & 7)) return MPHF_EINVAL;
+    if (!on_device(b->device)) return MPHF_EINVAL;
+    for (mphf_t *h : b->hs)
+        if (!h->plan) return MPHF_EINVAL;
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (zero_shared(b->size_hist, b->size_cursor, b->head, b->steal, st) != MPHF_OK)
+        return MPHF_ECUDA;
+    for (uint32_t i = 0; i < count; i++) {
+        if (zero_build(b->hs[i], st) != MPHF_OK) return MPHF_ECUDA;
+        enqueue_front(b->hs[i], d_keys[i], b->size_hist, st);
+    }
+    // one work order over the buckets of all builds, largest first
+    launch_exclusive_scan(b->size_hist, 4098, b->scan_tmp, st);
+    for (uint32_t i = 0; i < count; i++)
+        launch_items_by_size(b->hs[i]->cum_keys, b->hs[i]->plan->nb, b->size_hist, b->size_cursor,
+                             b->items, i, st);
+    launch_search(b->d_inst, count, b->items, (uint32_t)b->slots, b->head, b->L, b->steal, st);
+    for (mphf_t *h : b->hs) enqueue_back(h, st);
+    launch_gather_totals(b->src, count, b->totals, st);
+    return cudaGetLastError() == cudaSuccess ? MPHF_OK : MPHF_ECUDA;
+}
+
+int mphf_batch_finish(mphf_batch_t *b, void *stream, int *statuses) {
+    if (!b) return MPHF_EINVAL;
+    const uint32_t count = (uint32_t)b->hs.size();
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(b->host, b->totals, 16ull * count * 8, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
+    }
+    int first = MPHF_OK;
+    for (uint32_t i = 0; i < count; i++) {
+        const int rc = finish_from(b->hs[i], b->host + 16ull * i);
+        if (statuses) statuses[i] = rc;
+        if (rc && first == MPHF_OK) first = rc;
+    }
+    return first;
+}
+
+int mphf_batch_free(mphf_batch_t *b) {
+    if (!b) return MPHF_EINVAL;
+    int prev = -1;
+    const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+    cudaGetLastError();
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ECUDA;
+    }
+    release_batch(b);
+    if (have_prev) cudaSetDevice(prev);
     return MPHF_OK;
 }
 

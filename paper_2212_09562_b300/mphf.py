@@ -165,6 +165,10 @@ SIGNATURES = {
     "mphf_build_prepare": (_I, [_U64, _P, _U64, _P]),
     "mphf_build_enqueue": (_I, [_P, _P, _P]),
     "mphf_build_finish": (_I, [_P, _P]),
+    "mphf_batch_prepare": (_I, [_P, _U32, _U32, _U32, _P, _P]),
+    "mphf_batch_enqueue": (_I, [_P, _P, _P]),
+    "mphf_batch_finish": (_I, [_P, _P, _P]),
+    "mphf_batch_free": (_I, [_P]),
     "mphf_shard_route": (_I, [_P, _U64, _U32, _U64, _U32, _U32, _P, _P, _P]),
     "mphf_build_shard": (_I, [_P, _U64, _U64, _P, _U32, _U32, _P, _P]),
     "mphf_shard_pack": (_I, [_P, _P, _P, _P]),
@@ -500,6 +504,57 @@ def build_batch(keys_list, leaf_sizes, bucket_size: int = 2000, rotation=True,
                 lib().mphf_free(ctypes.c_void_p(outs[i]))
         _check(rc, "mphf_build_batch")
     return [MPHF(outs[i]) for i in range(count)]
+
+
+class PreparedBatch:
+    """Prepared builds (MPHF.prepare) searched by one persistent launch
+    (mphf_batch_*): enqueue(keys_list) issues all of them without allocation
+    or host synchronisation (capturable in a CUDA graph), finish() makes every
+    member usable.  The members stay owned by the caller and must outlive the
+    batch."""
+
+    def __init__(self, members, threads: int = 0, blocks_per_sm: int = 0):
+        _torch()
+        self.members = list(members)
+        count = len(self.members)
+        hs = (ctypes.c_void_p * max(count, 1))(*[m._h.value for m in self.members])
+        b = ctypes.c_void_p()
+        _check(lib().mphf_batch_prepare(hs, count, threads, blocks_per_sm, None, ctypes.byref(b)),
+               "mphf_batch_prepare")
+        self._b = b
+        self._ptrs = (ctypes.c_void_p * max(count, 1))()
+
+    def enqueue(self, keys_list, stream=None):
+        """Issues every member's build from keys_list[i] (its prepared n and key size)."""
+        if len(keys_list) != len(self.members):
+            raise ValueError("one key set per member")
+        for i, (m, k) in enumerate(zip(self.members, keys_list)):
+            n, kb = key_layout(k)
+            if n != m.info.n or kb != m.info.key_bytes:
+                raise ValueError(f"keys of member {i} must be its prepared number and size")
+            self._ptrs[i] = k.data_ptr()
+        _check(lib().mphf_batch_enqueue(self._b, self._ptrs, _stream(stream)), "mphf_batch_enqueue")
+
+    def finish(self, stream=None) -> list[int]:
+        """Waits and finishes every member; returns their codes (raises if any failed)."""
+        count = len(self.members)
+        sts = (ctypes.c_int * max(count, 1))()
+        rc = lib().mphf_batch_finish(self._b, _stream(stream), sts)
+        for m in self.members:
+            _check(lib().mphf_get_info(m._h, ctypes.byref(m.info)), "mphf_get_info")
+        _check(rc, "mphf_batch_finish")
+        return [sts[i] for i in range(count)]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mphf_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -109,3 +109,19 @@ def test_failing_build_and_recovery(torch):
     h.enqueue(dk)  # the same handle builds again
     h.finish()
     same(h, M.MPHF.build(dk, 8, 100, True))
+
+
+def test_enqueue_after_a_plain_build_of_smaller_buckets(torch):
+    """A plain build of small buckets between two enqueues must not leave the
+    search kernel's shared-memory limit below what the prepared build
+    launches with (room for the largest bucket a build accepts)."""
+    n = 20_000
+    dk = to_dev(torch, W.distinct_u64(n, 8450))
+    h = M.MPHF.prepare(n, 8, 100, True)
+    h.enqueue(dk)
+    h.finish()
+    small = M.MPHF.build(to_dev(torch, W.distinct_u64(500, 8451)), 8, 10, True)
+    assert small.info.n == 500
+    h.enqueue(dk)
+    h.finish()
+    same(h, M.MPHF.build(dk, 8, 100, True))

@@ -101,6 +101,17 @@ def test_handle_calls_reject_null_handles_and_misaligned_keys(lib):
     assert lib.mphf_server_destroy(None) == M.EINVAL
     assert lib.mphf_build_batch(None, 0, None, None, None) == M.OK  # an empty batch
     assert lib.mphf_build_batch(None, 2, None, None, None) == M.EINVAL
+    # prepared batches: checked before any device call
+    out = ctypes.c_void_p(1)
+    assert lib.mphf_batch_prepare(None, 1, 0, 0, None, ctypes.byref(out)) == M.EINVAL
+    assert out.value is None
+    fake = (ctypes.c_void_p * 1)(8)
+    assert lib.mphf_batch_prepare(fake, 0, 0, 0, None, ctypes.byref(out)) == M.EINVAL
+    assert lib.mphf_batch_prepare(fake, 1, 100, 0, None, ctypes.byref(out)) == M.EINVAL
+    assert lib.mphf_batch_prepare(fake, 1, 0, 0, None, None) == M.EINVAL
+    assert lib.mphf_batch_enqueue(None, None, None) == M.EINVAL
+    assert lib.mphf_batch_finish(None, None, None) == M.EINVAL
+    assert lib.mphf_batch_free(None) == M.EINVAL
     # keys must be 8-byte aligned: checked on the host, before any device work
     h = ctypes.c_void_p()
     assert lib.mphf_build_ex(12, 5, ctypes.byref(M.default_params()), None,
