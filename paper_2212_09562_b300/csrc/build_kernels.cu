@@ -361,6 +361,28 @@ struct HelpCtx {
 constexpr uint32_t kStealReady = 1u << 31;
 constexpr uint32_t kHelpMarker = 0xFFFFFFFEu;  // a steal item inviting a block to a shared search
 
+// Quotient-indexed counter increments of the full lower nodes of the
+// compiled leaf sizes (see DivShift): for leaf size l, fanouts f1, f2 and
+// nodes L1 = f1 l, L2 = f2 L1, a table of L1 >> ctz(l) entries (lower-1
+// nodes, unit l) and one of L2 >> ctz(L1) entries (lower-2 nodes, unit L1).
+__host__ __device__ constexpr uint32_t ctz_ce(uint32_t x) { return (x & 1u) ? 0u : 1u + ctz_ce(x >> 1); }
+__host__ __device__ constexpr uint32_t fan1_ce(uint32_t l) { return (35u * l + 154u) / 100u < 2 ? 2 : (35u * l + 154u) / 100u; }
+__host__ __device__ constexpr uint32_t fan2_ce(uint32_t l) { return (21u * l + 189u) / 100u < 2 ? 2 : (21u * l + 189u) / 100u; }
+__host__ __device__ constexpr uint32_t lutq_len(uint32_t l, int level) {
+    return level == 1 ? (fan1_ce(l) * l) >> ctz_ce(l)
+                      : (fan2_ce(l) * fan1_ce(l) * l) >> ctz_ce(fan1_ce(l) * l);
+}
+// The leaf sizes with compiled paths (the cases of the kernels' leaf switch),
+// in table order: 8, 12, 16; lutq_off of any other size is the total.
+__host__ __device__ constexpr uint32_t lutq_pair(uint32_t l) { return lutq_len(l, 1) + lutq_len(l, 2); }
+__host__ __device__ constexpr uint32_t lutq_off(uint32_t l, int level) {
+    return (l == 8 ? 0u : l == 12 ? lutq_pair(8) : l == 16 ? lutq_pair(8) + lutq_pair(12)
+                                               : lutq_pair(8) + lutq_pair(12) + lutq_pair(16)) +
+           ((l == 8 || l == 12 || l == 16) && level == 2 ? lutq_len(l, 1) : 0u);
+}
+constexpr uint32_t kLutQ = 128;
+static_assert(lutq_off(0, 1) <= kLutQ, "quotient tables too small");
+
 struct BlockState {
     uint16_t st_off[STACK], st_m[STACK], st_pidx[STACK];
     uint8_t st_depth[STACK];
@@ -373,6 +395,10 @@ struct BlockState {
     uint32_t cnt[16];
     unsigned long long lut64[16];  // child -> counter increment (last child: 0)
     uint32_t lut32[16];
+    // full lower nodes of a compiled leaf size, unit U = 2^a b: the increment
+    // by p >> a instead of by the child p / U = (p >> a) / b (see DivShift)
+    unsigned long long lutq64[kLutQ];
+    uint32_t lutq32[kLutQ];
 };
 
 struct SmemArrays {
@@ -398,6 +424,14 @@ __host__ __device__ constexpr bool counter_fits32(uint32_t m, uint32_t w, uint32
 template <uint32_t U>
 struct DivCT {
     __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return p / U; }
+};
+// Position p of a full lower node to the index of its increment in S.lutq:
+// p >> a for a unit U = 2^a b.  The child is p / U = (p >> a) / b (floor of
+// a floor), so the table holds the increment of child q / b at index q, and
+// no division by b is left in the search loop.
+template <uint32_t A>
+struct DivShift {
+    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return p >> A; }
 };
 struct DivRT {
     uint32_t magic;
@@ -1201,19 +1235,22 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
             using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
             // seeds per thread from the descriptor (the autotuner's choice)
+            constexpr uint32_t a1 = ctz_ce(LEAF), a2 = ctz_ce(L1);
             if (m == L1) {
-                const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
+                const C1 *lut = n1 ? (const C1 *)(S.lutq32 + lutq_off(LEAF, 1)) : (const C1 *)(S.lutq64 + lutq_off(LEAF, 1));
                 const auto mod = make_modct<L1>(d.red[1]);
-                x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S, share)
-                  : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S, share)
-                               : search_lower<1, C1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, mx, d.max_value, limit, S, share);
+                const DivShift<a1> dv{};
+                x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share)
+                  : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share)
+                               : search_lower<1, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share);
                 done = true;
             } else if (m == L2) {
-                const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
+                const C2 *lut = n2 ? (const C2 *)(S.lutq32 + lutq_off(LEAF, 2)) : (const C2 *)(S.lutq64 + lutq_off(LEAF, 2));
                 const auto mod = make_modct<L2>(d.red[2]);
-                x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S, share)
-                  : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S, share)
-                               : search_lower<1, C2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, mx, d.max_value, limit, S, share);
+                const DivShift<a2> dv{};
+                x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share)
+                  : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share)
+                               : search_lower<1, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share);
                 done = true;
             }
         }
@@ -1514,18 +1551,20 @@ __device__ __forceinline__ void help_node(const InstDesc &d, HelpRec *rec, uint3
         using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
         using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
         const uint64_t *xs = A.tlo;
+        const DivShift<ctz_ce(LEAF)> dv1{};
+        const DivShift<ctz_ce(L1)> dv2{};
         if (d.tree == MPHF_TREE_RECSPLIT && m == L1) {
-            const C1 *lut = n1 ? (const C1 *)S.lut32 : (const C1 *)S.lut64;
+            const C1 *lut = n1 ? (const C1 *)(S.lutq32 + lutq_off(LEAF, 1)) : (const C1 *)(S.lutq64 + lutq_off(LEAF, 1));
             const auto mod = make_modct<L1>(d.red[1]);
-            if (d.spt == 4) shared_rounds<4>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, d.max_value, rec, gen, false, S);
-            else if (d.spt == 2) shared_rounds<2>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, d.max_value, rec, gen, false, S);
-            else shared_rounds<1>(xs, m, mod, DivCT<LEAF>(), lut, (C1)expected, d.max_value, rec, gen, false, S);
+            if (d.spt == 4) shared_rounds<4>(xs, m, mod, dv1, lut, (C1)expected, d.max_value, rec, gen, false, S);
+            else if (d.spt == 2) shared_rounds<2>(xs, m, mod, dv1, lut, (C1)expected, d.max_value, rec, gen, false, S);
+            else shared_rounds<1>(xs, m, mod, dv1, lut, (C1)expected, d.max_value, rec, gen, false, S);
         } else if (d.tree == MPHF_TREE_RECSPLIT && m == L2) {
-            const C2 *lut = n2 ? (const C2 *)S.lut32 : (const C2 *)S.lut64;
+            const C2 *lut = n2 ? (const C2 *)(S.lutq32 + lutq_off(LEAF, 2)) : (const C2 *)(S.lutq64 + lutq_off(LEAF, 2));
             const auto mod = make_modct<L2>(d.red[2]);
-            if (d.spt == 4) shared_rounds<4>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, d.max_value, rec, gen, false, S);
-            else if (d.spt == 2) shared_rounds<2>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, d.max_value, rec, gen, false, S);
-            else shared_rounds<1>(xs, m, mod, DivCT<L1>(), lut, (C2)expected, d.max_value, rec, gen, false, S);
+            if (d.spt == 4) shared_rounds<4>(xs, m, mod, dv2, lut, (C2)expected, d.max_value, rec, gen, false, S);
+            else if (d.spt == 2) shared_rounds<2>(xs, m, mod, dv2, lut, (C2)expected, d.max_value, rec, gen, false, S);
+            else shared_rounds<1>(xs, m, mod, dv2, lut, (C2)expected, d.max_value, rec, gen, false, S);
         }
     }
     __syncthreads();
@@ -1600,6 +1639,30 @@ struct SmemLayout {
 // The persistent search (the brute-force searches of Section 2.2 in the
 // parallel form of Section 5.3): blocks take buckets from a device queue,
 // largest first, and run process_bucket on each.
+// All quotient-indexed increment tables of one block (before its first
+// barrier, once per launch).
+template <uint32_t UNIT, uint32_t NP, uint32_t M>
+__device__ __forceinline__ void fill_lutq(BlockState &S, uint32_t off) {
+    constexpr uint32_t a = ctz_ce(UNIT), b = UNIT >> a, w = field_width(UNIT);
+    for (uint32_t q = threadIdx.x; q < (M >> a); q += blockDim.x) {
+        const uint32_t c = q / b;
+        const uint64_t inc = c + 1 < NP ? 1ull << (w * c) : 0;  // the last child is implied
+        S.lutq64[off + q] = inc;
+        S.lutq32[off + q] = (uint32_t)inc;
+    }
+}
+template <uint32_t LEAF>
+__device__ __forceinline__ void fill_lutq_leaf(BlockState &S) {
+    constexpr uint32_t f1 = fan1_ce(LEAF), f2 = fan2_ce(LEAF), L1 = f1 * LEAF, L2 = f2 * L1;
+    fill_lutq<LEAF, f1, L1>(S, lutq_off(LEAF, 1));
+    fill_lutq<L1, f2, L2>(S, lutq_off(LEAF, 2));
+}
+__device__ __forceinline__ void init_lutq(BlockState &S) {
+    fill_lutq_leaf<8>(S);
+    fill_lutq_leaf<12>(S);
+    fill_lutq_leaf<16>(S);
+}
+
 __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, uint32_t ninst, const WorkItem *items,
                                                 uint32_t nitems, uint32_t *head, uint32_t cap,
                                                 StealQueue *steal, uint32_t steal_cap) {
@@ -1615,6 +1678,7 @@ __global__ void __launch_bounds__(512) k_search(const InstDesc *insts, uint32_t 
     A.leaf_pidx = A.leaf_off + lay.nl;
     A.leaf_m = (uint8_t *)(A.leaf_pidx + lay.nl);
     const StealCtx X{steal, head, nitems, steal_cap};
+    init_lutq(S);  // published by the first barrier below
     for (;;) {
         if (threadIdx.x == 0) {
             S.item = atomicAdd(head, 1u);
@@ -1750,6 +1814,7 @@ __global__ void __launch_bounds__(512) k_serve(const InstDesc *insts, const Work
         const uint32_t before = atomicAdd(&sm_count[smid & (kServeMaxSms - 1)], 1u);
         S.item = smid < reserved_sms && before >= 1;
     }
+    init_lutq(S);  // published by the barrier below
     __syncthreads();
     if (S.item) return;
     for (;;) {
