@@ -37,27 +37,28 @@ WORKLOAD = "rot_l16"
 # Integer-multiply (IMAD pipe) work of one key-hash evaluation at a full
 # lower-level node, by instruction form: the two 64 x 64 -> 64-bit multiplies
 # of the SplitMix64 remix on 32-bit lanes (each one 32 x 32 -> 64 wide
-# multiply-add and two 32-bit multiply-adds), the fold of h to 32 bits
-# congruent mod m (one wide multiply-add), and the remainder by the constant
-# node size (one multiply-high, one multiply-subtract).  Each form is weighted
-# by its issue cost relative to mad.lo.u32, measured in the same run by the
+# multiply-add and two 32-bit multiply-adds), and the remainder of the digit
+# sum that gives the child's counter index (h >> a) mod D (one multiply-high,
+# one multiply-subtract; D = 7 and 35 at l = 16).  Each form is weighted by
+# its issue cost relative to mad.lo.u32, measured in the same run by the
 # integer microbenchmark (peaks/int_peaks.cu).
-IMAD_FORMS_PER_EVAL = {"mad.wide.u32": 3, "mad.lo.u32": 5, "mad.hi.u32": 1}
+IMAD_FORMS_PER_EVAL = {"mad.wide.u32": 2, "mad.lo.u32": 5, "mad.hi.u32": 1}
 # All integer instructions one evaluation needs at least on 32-bit lanes:
 # 64-bit add (2), three 64-bit xor-shifts (4 each), two 64 x 64-bit multiplies
-# (3 each), exact remainder (3 multiply forms + 3 shift/add/carry), counter (3).
-OPS_PER_EVAL = 2 + 12 + 6 + 6 + 3
+# (3 each), the digits of h >> a and their sum (4), their remainder (2
+# multiply forms + 1 shift), the counter (table load and add, 2).
+OPS_PER_EVAL = 2 + 12 + 6 + 4 + 3 + 2
 # DRAM bytes the search kernel moves per key (lo word and rotation bit read
 # once per bucket, plus the keys of nodes given to other blocks), from
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_search
-# on 3,000,000 keys of rot_l16 (a multi-wave launch): 28,296,448 B.  The
+# on 3,000,000 keys of rot_l16 (a multi-wave launch): 28,251,136 B.  The
 # traffic of a launch grows with its key count.
-SEARCH_DRAM_BYTES_PER_KEY = 28_296_448 / 3_000_000
+SEARCH_DRAM_BYTES_PER_KEY = 28_251_136 / 3_000_000
 # Pipe utilisation of k_search over the elapsed cycles of the same capture
 # (sm__pipe_fmaheavy_cycles_active, sm__pipe_alu_cycles_active,
 # smsp__issue_active; .avg.pct_of_peak_sustained_elapsed).
-SEARCH_NCU_PIPES = {"fmaheavy_busy_of_elapsed": 0.814, "alu_busy_of_elapsed": 0.747,
-                    "issue_busy_of_elapsed": 0.735,
+SEARCH_NCU_PIPES = {"fmaheavy_busy_of_elapsed": 0.643, "alu_busy_of_elapsed": 0.791,
+                    "issue_busy_of_elapsed": 0.681, "instructions_per_eval": 31.6,
                     "capture": "ncu, k_search on 3e6 keys of rot_l16 (multi-wave), current kernel"}
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 

@@ -414,10 +414,7 @@ int phase_scatter(std::vector<Job *> &jobs, EngineCtx &c) {
         d.bij = j.p.leaf_bijection;
         d.tree = j.p.tree_shape;
         d.nb = (uint32_t)j.nb;
-        Shape shp = make_shape(j.p.leaf_size);
-        d.red[0] = (uint32_t)((1ull << 32) % j.p.leaf_size);
-        d.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
-        d.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
+        d.red_leaf = (uint32_t)((1ull << 32) % j.p.leaf_size);
         d.leaf_method = j.p.leaf_method;
         d.spt = j.p.seeds_per_thread ? j.p.seeds_per_thread : (j.p.leaf_size >= 16 ? 2u : 1u);
         d.mod_c = h->tabs.mod_c;

@@ -399,6 +399,7 @@ struct BlockState {
     // by p >> a instead of by the child p / U = (p >> a) / b (see DivShift)
     unsigned long long lutq64[kLutQ];
     uint32_t lutq32[kLutQ];
+    InstDesc desc;  // the serving search's current request (read at L2 by load_desc_shared)
 };
 
 struct SmemArrays {
@@ -489,6 +490,71 @@ __device__ __forceinline__ uint32_t mod_halves(const ModCTR<MM> &r, uint32_t hl,
         return v % MM;
     }
 }
+// The increment index of a full lower node straight from the hash, with no
+// 64-bit remainder.  For a node of MM keys in parts of U = 2^A b keys the
+// split search needs only p >> A, p = h mod MM (its entry in S.lutq).  As
+// 2^A divides MM, p >> A = y mod D with y = h >> A and D = MM >> A.  Write
+// D = 2^t D' (D' odd): y mod D = 2^t ((y >> t) mod D') + (y mod 2^t).  For
+// z = y >> t, with k a multiple of the order e of 2 modulo D' (2^e = 1 mod
+// D'), 2^k = 1 (mod D'), so z mod D' is the sum of z's k-bit digits mod D'
+// (the digits taken from the two 32-bit halves of h at fixed bit positions).
+// At l = 16: D = 7 (lower-1, two 30-bit digits) and 35 (lower-2, three
+// 24-bit digits); at l = 12: 15 and 4 * 15 (32-bit digits, the carry of
+// their sum folded back since 2^32 = 1 mod 15); at l = 8: 4 and 3.
+__host__ __device__ constexpr uint32_t ord2_ce(uint32_t d, uint32_t e = 1, uint32_t p = 2) {
+    return d <= 1 ? 1 : (p % d == 1 ? e : ord2_ce(d, e + 1, (p * 2) % d));
+}
+// Bits [POS, POS + W) of h = hh 2^32 + hl (W <= 32, POS + W <= 64).
+template <uint32_t POS, uint32_t W>
+__device__ __forceinline__ uint32_t bits_of(uint32_t hl, uint32_t hh) {
+    static_assert(W >= 1 && W <= 32 && POS + W <= 64, "bit field out of range");
+    uint32_t v;
+    if constexpr (POS >= 32) v = hh >> (POS - 32);
+    else if constexpr (POS == 0) v = hl;
+    else v = __funnelshift_r(hl, hh, POS);  // low word of h >> POS
+    if constexpr (W < 32) v &= (1u << W) - 1u;
+    return v;
+}
+template <uint32_t MM, uint32_t A>
+struct QIdx {
+    static constexpr uint32_t D = MM >> A;
+    static constexpr uint32_t t = ctz_ce(D);
+    static constexpr uint32_t Dp = D >> t;  // odd part
+    static constexpr uint32_t Z = A + t;    // z = h >> Z
+    static constexpr uint32_t e = ord2_ce(Dp);
+    static constexpr uint32_t k = (32 / e) * e;  // digit width
+    static_assert(((MM >> A) << A) == MM, "2^A must divide the node size");
+    static_assert(Dp == 1 || e <= 32, "no digit width for this modulus");
+};
+template <uint32_t MM, uint32_t A>
+__device__ __forceinline__ uint32_t mod_halves(const QIdx<MM, A> &, uint32_t hl, uint32_t hh) {
+    using Q = QIdx<MM, A>;
+    uint32_t r = 0;  // z mod D'
+    if constexpr (Q::Dp > 1) {
+        constexpr uint32_t Z = Q::Z, k = Q::k;
+        uint32_t s;
+        if constexpr (k == 32) {
+            // two digits (z has at most 64 bits); 2^32 = 1 (mod D'): a carry adds 1
+            const uint32_t d0 = bits_of<Z, (64 - Z < 32 ? 64 - Z : 32)>(hl, hh);
+            if constexpr (Z + 32 < 64) {
+                const uint32_t d1 = bits_of<Z + 32, 32 - Z>(hl, hh);
+                const uint32_t sum = d0 + d1;
+                s = sum + (sum < d0 ? 1u : 0u);  // no overflow: with a carry, sum <= 2^32 - 2
+            } else {
+                s = d0;
+            }
+        } else {
+            static_assert(64 - Z <= 3 * k && k <= 30, "digit sum must fit 32 bits");
+            s = bits_of<Z, k>(hl, hh);
+            if constexpr (Z + k < 64) s += bits_of<Z + k, (64 - Z - k < k ? 64 - Z - k : k)>(hl, hh);
+            if constexpr (Z + 2 * k < 64) s += bits_of<Z + 2 * k, 64 - Z - 2 * k>(hl, hh);
+        }
+        r = s % Q::Dp;
+    }
+    if constexpr (Q::t > 0) return (r << Q::t) | bits_of<A, Q::t>(hl, hh);
+    return r;
+}
+
 // The constant comes from the instance descriptor in device memory, so the
 // compiler cannot fold it back into an immediate.
 template <uint32_t MM>
@@ -1238,16 +1304,16 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             constexpr uint32_t a1 = ctz_ce(LEAF), a2 = ctz_ce(L1);
             if (m == L1) {
                 const C1 *lut = n1 ? (const C1 *)(S.lutq32 + lutq_off(LEAF, 1)) : (const C1 *)(S.lutq64 + lutq_off(LEAF, 1));
-                const auto mod = make_modct<L1>(d.red[1]);
-                const DivShift<a1> dv{};
+                const QIdx<L1, a1> mod{};  // the table index p >> a1 straight from the hash
+                const DivShift<0> dv{};
                 x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share)
                   : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share)
                                : search_lower<1, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share);
                 done = true;
             } else if (m == L2) {
                 const C2 *lut = n2 ? (const C2 *)(S.lutq32 + lutq_off(LEAF, 2)) : (const C2 *)(S.lutq64 + lutq_off(LEAF, 2));
-                const auto mod = make_modct<L2>(d.red[2]);
-                const DivShift<a2> dv{};
+                const QIdx<L2, a2> mod{};
+                const DivShift<0> dv{};
                 x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share)
                   : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share)
                                : search_lower<1, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share);
@@ -1362,8 +1428,8 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
             for (uint32_t i = 0; i < m; i++) bmask |= (uint32_t)A.bb[off + i] << i;
             if constexpr (LEAF != 0) {
                 if (m == (uint32_t)LEAF) {  // full leaf: compile-time m and modulus
-                    x = d.bij ? leaf_rotation<LEAF>(xs, bmask, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane)
-                                   : leaf_plain<LEAF>(xs, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane);
+                    x = d.bij ? leaf_rotation<LEAF>(xs, bmask, m, make_modct<LEAF>(d.red_leaf), mx, d.max_value, limit, lane)
+                                   : leaf_plain<LEAF>(xs, m, make_modct<LEAF>(d.red_leaf), mx, d.max_value, limit, lane);
                     done = true;
                 }
             }
@@ -1376,8 +1442,8 @@ __device__ __forceinline__ void leaf_phase(const InstDesc &d, uint64_t nbase, co
             const uint8_t *period = use_lut ? d.rot_period + ((1u << m) - 4) : nullptr;
             if constexpr (LEAF != 0) {
                 if (m == (uint32_t)LEAF) {
-                    x = d.bij ? leaf_cyclic<true>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, canon, period)
-                                   : leaf_cyclic<false>(xs, A.bb + off, m, make_modct<LEAF>(d.red[0]), mx, d.max_value, limit, lane, nullptr, nullptr);
+                    x = d.bij ? leaf_cyclic<true>(xs, A.bb + off, m, make_modct<LEAF>(d.red_leaf), mx, d.max_value, limit, lane, canon, period)
+                                   : leaf_cyclic<false>(xs, A.bb + off, m, make_modct<LEAF>(d.red_leaf), mx, d.max_value, limit, lane, nullptr, nullptr);
                     done = true;
                 }
             }
@@ -1551,17 +1617,16 @@ __device__ __forceinline__ void help_node(const InstDesc &d, HelpRec *rec, uint3
         using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
         using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
         const uint64_t *xs = A.tlo;
-        const DivShift<ctz_ce(LEAF)> dv1{};
-        const DivShift<ctz_ce(L1)> dv2{};
+        const DivShift<0> dv1{}, dv2{};
         if (d.tree == MPHF_TREE_RECSPLIT && m == L1) {
             const C1 *lut = n1 ? (const C1 *)(S.lutq32 + lutq_off(LEAF, 1)) : (const C1 *)(S.lutq64 + lutq_off(LEAF, 1));
-            const auto mod = make_modct<L1>(d.red[1]);
+            const QIdx<L1, ctz_ce(LEAF)> mod{};
             if (d.spt == 4) shared_rounds<4>(xs, m, mod, dv1, lut, (C1)expected, d.max_value, rec, gen, false, S);
             else if (d.spt == 2) shared_rounds<2>(xs, m, mod, dv1, lut, (C1)expected, d.max_value, rec, gen, false, S);
             else shared_rounds<1>(xs, m, mod, dv1, lut, (C1)expected, d.max_value, rec, gen, false, S);
         } else if (d.tree == MPHF_TREE_RECSPLIT && m == L2) {
             const C2 *lut = n2 ? (const C2 *)(S.lutq32 + lutq_off(LEAF, 2)) : (const C2 *)(S.lutq64 + lutq_off(LEAF, 2));
-            const auto mod = make_modct<L2>(d.red[2]);
+            const QIdx<L2, ctz_ce(L1)> mod{};
             if (d.spt == 4) shared_rounds<4>(xs, m, mod, dv2, lut, (C2)expected, d.max_value, rec, gen, false, S);
             else if (d.spt == 2) shared_rounds<2>(xs, m, mod, dv2, lut, (C2)expected, d.max_value, rec, gen, false, S);
             else shared_rounds<1>(xs, m, mod, dv2, lut, (C2)expected, d.max_value, rec, gen, false, S);
@@ -1783,14 +1848,15 @@ __device__ unsigned long long serve_claim(ServeCtl *c, unsigned long long idle_n
     return ~0ull;
 }
 
-__device__ __forceinline__ InstDesc load_desc(const InstDesc *p) {
+// A request's descriptor, written by the host while the kernel runs, is read
+// at L2 (never a stale L1 line of a reused slot) into shared memory by the
+// first threads; the caller's barrier publishes it.  Held there rather than in
+// registers, it leaves the search loops their registers.
+__device__ __forceinline__ void load_desc_shared(const InstDesc *p, InstDesc &out) {
     static_assert(sizeof(InstDesc) % 8 == 0, "descriptor is copied as 64-bit words");
-    InstDesc d;
     const unsigned long long *src = (const unsigned long long *)p;
-    unsigned long long *dst = (unsigned long long *)&d;
-#pragma unroll
-    for (uint32_t i = 0; i < sizeof(InstDesc) / 8; i++) dst[i] = __ldcg(src + i);
-    return d;
+    unsigned long long *dst = (unsigned long long *)&out;
+    if (threadIdx.x < sizeof(InstDesc) / 8) dst[threadIdx.x] = __ldcg(src + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(512) k_serve(const InstDesc *insts, const WorkItem *ring,
@@ -1825,7 +1891,9 @@ __global__ void __launch_bounds__(512) k_serve(const InstDesc *insts, const Work
         if (it == ~0ull) break;
         const unsigned long long raw = __ldcg((const unsigned long long *)(ring + it % ring_cap));
         const WorkItem w{(uint32_t)raw, (uint32_t)(raw >> 32)};
-        const InstDesc d = load_desc(insts + w.inst);
+        load_desc_shared(insts + w.inst, S.desc);  // every thread has left the previous bucket
+        __syncthreads();
+        const InstDesc &d = S.desc;
         switch (d.leaf) {
             case 8: process_bucket<8>(d, w.bucket, A, S); break;
             case 12: process_bucket<12>(d, w.bucket, A, S); break;

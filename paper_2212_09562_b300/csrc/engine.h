@@ -32,7 +32,7 @@ struct InstDesc {
     uint32_t leaf, bij;          // bij: MPHF_BIJECTION_* leaf method
     uint32_t tree;               // MPHF_TREE_*: lower aggregation levels or fanout 2 everywhere
     uint32_t nb;
-    uint32_t red[3];             // 2^32 mod m for full leaves, lower-1 and lower-2 nodes
+    uint32_t red_leaf;           // 2^32 mod l, for the remainders of full leaves
     uint32_t leaf_method;        // 0 lock-step, 1 early rejection, 2 early rejection + table
     uint32_t spt;                // seeds per thread of full lower-level split searches (1, 2, 4)
     const uint8_t *rot_canon;    // per m <= 16 at offset 2^m - 4: canonical rotation of x

@@ -334,10 +334,7 @@ int mphf_build_prepare(uint64_t n, const mphf_build_params *p, uint64_t gr_capac
     d.bij = p->leaf_bijection;
     d.tree = p->tree_shape;
     d.nb = (uint32_t)nb;
-    const Shape shp = make_shape(p->leaf_size);
-    d.red[0] = (uint32_t)((1ull << 32) % p->leaf_size);
-    d.red[1] = (uint32_t)((1ull << 32) % shp.lower1);
-    d.red[2] = (uint32_t)((1ull << 32) % shp.lower2);
+    d.red_leaf = (uint32_t)((1ull << 32) % p->leaf_size);
     d.leaf_method = p->leaf_method;
     d.spt = p->seeds_per_thread ? p->seeds_per_thread : (p->leaf_size >= 16 ? 2u : 1u);
     d.mod_c = h->tabs.mod_c;

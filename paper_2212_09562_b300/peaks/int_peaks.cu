@@ -16,10 +16,13 @@
 //   kind 5  mixed        one mad.lo.u32 and one lop3.b32 per step
 //   kind 6  evaluation   one key-hash evaluation of a lower-level split at
 //                        l = 16 (node of 112 keys, 7 children of 16): the
-//                        SplitMix64 remix, the exact remainder mod 112, the
-//                        child index and the packed counter update, keys
-//                        and counters in registers
+//                        SplitMix64 remix, the child index (h mod 112) / 16
+//                        = (h >> 4) mod 7 from the sum of two 30-bit digits
+//                        (2^30 = 1 mod 7), and the packed counter update,
+//                        keys and counters in registers
 //   kind 7  mul64        64 x 64 -> 64-bit multiply by a runtime constant
+//                        (mul.lo.u64 in inline PTX, so the chain stays one
+//                        multiply per step)
 //   kind 8  remix        the SplitMix64 output function on a 64-bit word
 //
 // Each timed launch also reads clock64 and %globaltimer in every block, so
@@ -80,7 +83,8 @@ __device__ __forceinline__ void step(uint32_t (&x)[2 * kChains], uint64_t (&w)[k
             asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x[c]) : "r"(a), "r"(b));
             asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[kChains + c]) : "r"(a), "r"(b));
         } else if constexpr (KIND == 7) {
-            w[c] *= ((uint64_t)b << 32) | a;
+            const uint64_t m = ((uint64_t)b << 32) | a;
+            asm volatile("mul.lo.u64 %0, %0, %1;" : "+l"(w[c]) : "l"(m));
         } else if constexpr (KIND == 8) {
             w[c] = remix(w[c]);
         }
@@ -116,10 +120,11 @@ __global__ void __launch_bounds__(512) k_peak(uint32_t a, uint32_t b, uint32_t i
 }
 
 // One evaluation of a lower-1 split of l = 16 per key and seed: h = remix(x +
-// s), v = a 32-bit value congruent to h mod 112 (2^32 = 32 mod 112), child =
-// (v mod 112) / 16, and the child's packed counter field incremented (the
-// last child's field implied, as in the build).
-__global__ void __launch_bounds__(512) k_eval(uint32_t c112, uint32_t iters, uint32_t *sink,
+// s), child = (h mod 112) / 16 = (h >> 4) mod 7, taken as the sum of the two
+// 30-bit digits of h >> 4 mod 7, and the child's packed counter field
+// incremented (the last child's field implied, as in the build).  mask30 is
+// 2^30 - 1, passed at run time like the build's table lookups.
+__global__ void __launch_bounds__(512) k_eval(uint32_t mask30, uint32_t iters, uint32_t *sink,
                                               unsigned long long *clk) {
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t key[kChains];
@@ -135,12 +140,9 @@ __global__ void __launch_bounds__(512) k_eval(uint32_t c112, uint32_t iters, uin
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 const uint64_t h = remix(key[c] + (uint64_t)(tid + (s + j) * 4096u));
-                const uint64_t t = (uint64_t)(uint32_t)(h >> 32) * c112 + (uint32_t)h;
-                const uint32_t th = (uint32_t)(t >> 32), tl = (uint32_t)t;
-                const uint32_t add = th << 5;
-                const uint32_t ul = tl + add;
-                const uint32_t v = ul + (ul < add ? 32u : 0u);
-                const uint32_t child = (v % 112u) / 16u;
+                const uint32_t hl = (uint32_t)h, hh = (uint32_t)(h >> 32);
+                const uint32_t d0 = __funnelshift_r(hl, hh, 4) & mask30, d1 = hh >> 2;
+                const uint32_t child = (d0 + d1) % 7u;
                 const uint32_t inc = child < 6 ? 1u << (5 * child) : 0u;
                 if (j == 0)
                     cnt0 += inc;
@@ -248,7 +250,7 @@ int ip_run(int kind, int reps, double target_ms, ip_result *out) {
             case 5: k_peak<5><<<blocks, threads>>>(3u, 7u, iters, sink, clk); break;
             case 7: k_peak<7><<<blocks, threads>>>(0x1CE4E5B9u, 0xBF58476Du, iters, sink, clk); break;
             case 8: k_peak<8><<<blocks, threads>>>(0u, 0u, iters, sink, clk); break;
-            default: k_eval<<<blocks, threads>>>(32u, iters, sink, clk); break;
+            default: k_eval<<<blocks, threads>>>((1u << 30) - 1u, iters, sink, clk); break;
         }
     };
     // calibrate the iteration count to about target_ms per launch
