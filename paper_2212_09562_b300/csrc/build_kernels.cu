@@ -457,11 +457,12 @@ __device__ __forceinline__ uint32_t mod_halves(const ModRT &r, uint32_t hl, uint
     uint32_t v = (uint32_t)(u >> 32) * r.c + (uint32_t)u;
     return (uint32_t)__umul64hi(r.M * v, r.m);
 }
-// Compile-time modulus with the reduction constant c = 2^32 mod MM held in a
-// register: for the benchmark node sizes c is a power of two (32 for 112,
-// 256 for 560), and as an immediate the compiler turns the wide multiply-adds
-// into 64-bit shift/add chains on the integer ALU pipe, the pipe the search
-// is bound by.  The last step v mod MM keeps the constant divisor.
+// Compile-time modulus (the full leaves) with the reduction constant
+// c = 2^32 mod MM held in a register, read from the instance descriptor so
+// that the compiler keeps the wide multiply-add on the IMAD pipe instead of
+// turning it into ALU shift/add chains.  A power-of-two MM (8, 16) is the low
+// bits of h; for MM = 12, c = 4 and the fold below applies.  The last step
+// v mod MM keeps the constant divisor.
 template <uint32_t MM>
 struct ModCTR {
     uint32_t c;
@@ -1292,7 +1293,8 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
         const bool share = S.hc.q != nullptr;
         bool done = false;
         if constexpr (LEAF != 0) {
-            // full lower-1 and lower-2 nodes: compile-time modulus, unit, counter width
+            // full lower-1 and lower-2 nodes: the counter index from a digit sum (QIdx),
+            // compile-time unit and counter width
             constexpr uint32_t f1 = ((35u * LEAF + 154u) / 100u) < 2 ? 2 : (35u * LEAF + 154u) / 100u;
             constexpr uint32_t f2 = ((21u * LEAF + 189u) / 100u) < 2 ? 2 : (21u * LEAF + 189u) / 100u;
             constexpr uint32_t L1 = f1 * LEAF, L2 = f2 * L1;

@@ -13,6 +13,15 @@
 // totals and the status and fills the handle's sizes, after which it is an
 // ordinary function (queries, serialisation, arrays) until the next enqueue.
 // The stored words are those of mphf_build_ex on the same keys.
+//
+// A batch (mphf_batch_*) runs many prepared builds through ONE persistent
+// search launch, as mphf_build_batch does: every member's plan counts its
+// buckets into the batch's size histogram, one work order covers all of them
+// largest first, and after the members' packing one kernel gathers every
+// member's status and totals into one array, so that finishing the batch is
+// one copy to the host.  The batch holds the launch's shared scratch; each
+// member keeps its own search scratch too (about 0.7 MB, mostly its steal
+// queue), unused while it builds inside a batch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
