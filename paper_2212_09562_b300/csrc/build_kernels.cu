@@ -40,6 +40,20 @@ __device__ __forceinline__ void load_key(const void *keys, uint64_t i, uint32_t 
     }
 }
 
+// The same with the streaming hint (evict first): keys read for the last
+// time, which should not push out of L2 the output lines still being filled.
+__device__ __forceinline__ void load_key_last(const void *keys, uint64_t i, uint32_t kb, uint64_t &w0,
+                                              uint64_t &w1) {
+    const uint64_t *p = (const uint64_t *)keys;
+    if (kb == 8) {
+        w0 = __ldcs(p + i);
+        w1 = 0;
+    } else {
+        w0 = __ldcs(p + 2 * i);
+        w1 = __ldcs(p + 2 * i + 1);
+    }
+}
+
 static unsigned long long g_launches = 0;
 void note_launches(uint64_t k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
 uint64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
@@ -92,6 +106,10 @@ void launch_fp_hist(const void *keys, uint64_t n, uint32_t key_bytes, uint64_t n
 // chunk and places keys through shared-memory cursors.  Global atomics drop
 // from one per key to one per bucket and block.
 constexpr uint32_t kSmemBuckets = 8192;
+// Keys a thread loads before it hashes any: the chunk loops are bound by
+// the latency of their key loads, so more loads in flight per thread raise
+// the bandwidth (one coalesced load per key position, as before).
+constexpr int kSortBatch = 4;
 
 __global__ void k_fp_hist_blk(const void *keys, uint64_t n, uint32_t kb, uint32_t nb, BucketRange R,
                               uint64_t chunk, unsigned long long *counts, uint32_t *blk,
@@ -100,11 +118,21 @@ __global__ void k_fp_hist_blk(const void *keys, uint64_t n, uint32_t kb, uint32_
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const uint64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
-    for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        uint64_t w0, w1, hi, lo, b;
-        load_key(keys, i, kb, w0, w1);
-        fingerprint(w0, w1, hi, lo);
-        if (local_bucket(R, hi, nb, status, b)) atomicAdd(&hist[b], 1u);
+    const uint64_t T = blockDim.x;
+    for (uint64_t i0 = beg + threadIdx.x; i0 < end; i0 += kSortBatch * T) {
+        uint64_t w0[kSortBatch], w1[kSortBatch];
+#pragma unroll
+        for (int u = 0; u < kSortBatch; u++) {
+            w0[u] = w1[u] = 0;
+            if (i0 + u * T < end) load_key(keys, i0 + u * T, kb, w0[u], w1[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kSortBatch; u++) {
+            if (i0 + u * T >= end) continue;
+            uint64_t hi, lo, b;
+            fingerprint(w0[u], w1[u], hi, lo);
+            if (local_bucket(R, hi, nb, status, b)) atomicAdd(&hist[b], 1u);
+        }
     }
     __syncthreads();
     uint32_t *row = blk + (uint64_t)blockIdx.x * nb;
@@ -146,14 +174,24 @@ __global__ void k_scatter_blk(const void *keys, uint64_t n, uint32_t kb, uint32_
     for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cursor[b] = row[b];
     __syncthreads();
     const uint64_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
-    for (uint64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        uint64_t w0, w1, hi, lo, b;
-        load_key(keys, i, kb, w0, w1);
-        fingerprint(w0, w1, hi, lo);
-        if (!local_bucket(R, hi, nb, status, b)) continue;
-        const uint32_t p = atomicAdd(&cursor[b], 1u);
-        lo_out[p] = lo;
-        bb_out[p] = (uint8_t)(hi & 1);
+    const uint64_t T = blockDim.x;
+    for (uint64_t i0 = beg + threadIdx.x; i0 < end; i0 += kSortBatch * T) {
+        uint64_t w0[kSortBatch], w1[kSortBatch];
+#pragma unroll
+        for (int u = 0; u < kSortBatch; u++) {
+            w0[u] = w1[u] = 0;
+            if (i0 + u * T < end) load_key_last(keys, i0 + u * T, kb, w0[u], w1[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kSortBatch; u++) {
+            if (i0 + u * T >= end) continue;
+            uint64_t hi, lo, b;
+            fingerprint(w0[u], w1[u], hi, lo);
+            if (!local_bucket(R, hi, nb, status, b)) continue;
+            const uint32_t p = atomicAdd(&cursor[b], 1u);
+            lo_out[p] = lo;
+            bb_out[p] = (uint8_t)(hi & 1);
+        }
     }
 }
 
