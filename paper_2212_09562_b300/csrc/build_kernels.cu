@@ -486,6 +486,13 @@ struct Mixer {
         hl = (uint32_t)h;
         hh = (uint32_t)(h >> 32);
     }
+    // the halves of y = mix64_pre(z), for reductions that read the bits of
+    // h = y ^ (y >> 31) they need straight from y (QIdx)
+    __device__ __forceinline__ void pre(uint64_t z, uint32_t &yl, uint32_t &yh) const {
+        const uint64_t y = mix64_pre(z);
+        yl = (uint32_t)y;
+        yh = (uint32_t)(y >> 32);
+    }
 };
 
 // h mod m from the halves of h (same reduction as ModRT / ModCT).
@@ -543,14 +550,22 @@ __device__ __forceinline__ uint32_t mod_halves(const ModCTR<MM> &r, uint32_t hl,
 __host__ __device__ constexpr uint32_t ord2_ce(uint32_t d, uint32_t e = 1, uint32_t p = 2) {
     return d <= 1 ? 1 : (p % d == 1 ? e : ord2_ce(d, e + 1, (p * 2) % d));
 }
-// Bits [POS, POS + W) of h = hh 2^32 + hl (W <= 32, POS + W <= 64).
+// The low word of y >> POS, y = yh 2^32 + yl (POS < 64).
+template <uint32_t POS>
+__device__ __forceinline__ uint32_t word_at(uint32_t yl, uint32_t yh) {
+    if constexpr (POS >= 32) return yh >> (POS - 32);
+    else if constexpr (POS == 0) return yl;
+    else return __funnelshift_r(yl, yh, POS);
+}
+// Bits [POS, POS + W) of h = y ^ (y >> 31) (the remix's last xor-shift),
+// read from y: bit i of h is y_i ^ y_(i+31), so a field of h is the field of
+// y xor the field 31 bits higher (zero past bit 63), and h itself is never
+// formed (W <= 32, POS + W <= 64).
 template <uint32_t POS, uint32_t W>
-__device__ __forceinline__ uint32_t bits_of(uint32_t hl, uint32_t hh) {
+__device__ __forceinline__ uint32_t hbits_of(uint32_t yl, uint32_t yh) {
     static_assert(W >= 1 && W <= 32 && POS + W <= 64, "bit field out of range");
-    uint32_t v;
-    if constexpr (POS >= 32) v = hh >> (POS - 32);
-    else if constexpr (POS == 0) v = hl;
-    else v = __funnelshift_r(hl, hh, POS);  // low word of h >> POS
+    uint32_t v = word_at<POS>(yl, yh);
+    if constexpr (POS + 31 < 64) v ^= word_at<POS + 31>(yl, yh);
     if constexpr (W < 32) v &= (1u << W) - 1u;
     return v;
 }
@@ -565,8 +580,10 @@ struct QIdx {
     static_assert(((MM >> A) << A) == MM, "2^A must divide the node size");
     static_assert(Dp == 1 || e <= 32, "no digit width for this modulus");
 };
+// The index from the halves of y = mix64_pre(x + s) (round_counts passes y,
+// not h, for this reduction; see hbits_of).
 template <uint32_t MM, uint32_t A>
-__device__ __forceinline__ uint32_t mod_halves(const QIdx<MM, A> &, uint32_t hl, uint32_t hh) {
+__device__ __forceinline__ uint32_t mod_halves(const QIdx<MM, A> &, uint32_t yl, uint32_t yh) {
     using Q = QIdx<MM, A>;
     uint32_t r = 0;  // z mod D'
     if constexpr (Q::Dp > 1) {
@@ -574,9 +591,9 @@ __device__ __forceinline__ uint32_t mod_halves(const QIdx<MM, A> &, uint32_t hl,
         uint32_t s;
         if constexpr (k == 32) {
             // two digits (z has at most 64 bits); 2^32 = 1 (mod D'): a carry adds 1
-            const uint32_t d0 = bits_of<Z, (64 - Z < 32 ? 64 - Z : 32)>(hl, hh);
+            const uint32_t d0 = hbits_of<Z, (64 - Z < 32 ? 64 - Z : 32)>(yl, yh);
             if constexpr (Z + 32 < 64) {
-                const uint32_t d1 = bits_of<Z + 32, 32 - Z>(hl, hh);
+                const uint32_t d1 = hbits_of<Z + 32, 32 - Z>(yl, yh);
                 const uint32_t sum = d0 + d1;
                 s = sum + (sum < d0 ? 1u : 0u);  // no overflow: with a carry, sum <= 2^32 - 2
             } else {
@@ -584,15 +601,20 @@ __device__ __forceinline__ uint32_t mod_halves(const QIdx<MM, A> &, uint32_t hl,
             }
         } else {
             static_assert(64 - Z <= 3 * k && k <= 30, "digit sum must fit 32 bits");
-            s = bits_of<Z, k>(hl, hh);
-            if constexpr (Z + k < 64) s += bits_of<Z + k, (64 - Z - k < k ? 64 - Z - k : k)>(hl, hh);
-            if constexpr (Z + 2 * k < 64) s += bits_of<Z + 2 * k, 64 - Z - 2 * k>(hl, hh);
+            s = hbits_of<Z, k>(yl, yh);
+            if constexpr (Z + k < 64) s += hbits_of<Z + k, (64 - Z - k < k ? 64 - Z - k : k)>(yl, yh);
+            if constexpr (Z + 2 * k < 64) s += hbits_of<Z + 2 * k, 64 - Z - 2 * k>(yl, yh);
         }
         r = s % Q::Dp;
     }
-    if constexpr (Q::t > 0) return (r << Q::t) | bits_of<A, Q::t>(hl, hh);
+    if constexpr (Q::t > 0) return (r << Q::t) | hbits_of<A, Q::t>(yl, yh);
     return r;
 }
+// Reductions that take y = mix64_pre(x + s) instead of the hash itself.
+template <class M>
+struct TakesPre : std::false_type {};
+template <uint32_t MM, uint32_t A>
+struct TakesPre<QIdx<MM, A>> : std::true_type {};
 
 // The constant comes from the instance descriptor in device memory, so the
 // compiler cannot fold it back into an immediate.
@@ -630,7 +652,10 @@ __device__ __forceinline__ void round_counts(const uint64_t *xs, uint32_t m, Mod
 #pragma unroll
         for (int j = 0; j < SPT; j++) {
             uint32_t hl, hh;
-            mx(x + s0 + (uint64_t)j * T, hl, hh);
+            if constexpr (TakesPre<Mod>::value)
+                mx.pre(x + s0 + (uint64_t)j * T, hl, hh);
+            else
+                mx(x + s0 + (uint64_t)j * T, hl, hh);
             cnt[j] += lut[div(mod_halves(mod, hl, hh))];
         }
     };

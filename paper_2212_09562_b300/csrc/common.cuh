@@ -27,13 +27,17 @@ namespace rs {
 
 // The remix of the node hash (Section 2.2, "a hash function modulo l"):
 // the SplitMix64 output function of Steele, Lea and Flood (OOPSLA 2014).
-__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+// mix64 without its last xor-shift: mix64(z) = y ^ (y >> 31), y = mix64_pre(z).
+__host__ __device__ __forceinline__ uint64_t mix64_pre(uint64_t z) {
     z ^= z >> 30;
     z *= 0xBF58476D1CE4E5B9ull;
     z ^= z >> 27;
     z *= 0x94D049BB133111EBull;
-    z ^= z >> 31;
     return z;
+}
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = mix64_pre(z);
+    return z ^ (z >> 31);
 }
 
 // The master hash code of a key (Section 2.2, the initial hash; Section 6

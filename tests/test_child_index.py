@@ -1,5 +1,7 @@
 """The split search's child index for full lower nodes, without a 64-bit
-remainder (the digit-sum identity of the search kernel), checked on the host.
+remainder (the digit-sum identity of the search kernel), checked on the host;
+also in the form the kernel evaluates it, with the digits of the hash read
+from the remix's value before its last xor-shift.
 
 A full lower node of MM keys has parts of U = 2^a b keys; the search needs
 p >> a for p = h mod MM.  As 2^a divides MM, p >> a = (h >> a) mod D with
@@ -37,7 +39,17 @@ def bits(h, pos, width):
     return (h >> pos) & ((1 << width) - 1)
 
 
-def child_index(h, mm, a):
+def hbits_from_pre(y, pos, width):
+    """Bits [pos, pos + width) of h = y ^ (y >> 31) (the remix's last
+    xor-shift) read from y as the kernel does: the field of y xor the field
+    31 bits higher, zero past bit 63."""
+    v = (y >> pos) & 0xFFFFFFFF
+    if pos + 31 < 64:
+        v ^= (y >> (pos + 31)) & 0xFFFFFFFF
+    return v & ((1 << width) - 1)
+
+
+def child_index(h, mm, a, field=bits):
     """The kernel's steps: digits of h >> z (z = a + t) of k bits, their sum
     (with the carry of two 32-bit digits added back), its remainder mod D',
     and the low t bits of h >> a below it."""
@@ -50,24 +62,24 @@ def child_index(h, mm, a):
     r = 0
     if dp > 1:
         if k == 32:
-            d0 = bits(h, z, min(64 - z, 32))
+            d0 = field(h, z, min(64 - z, 32))
             if z + 32 < 64:
-                s = d0 + bits(h, z + 32, 32 - z)
+                s = d0 + field(h, z + 32, 32 - z)
                 if s >= 1 << 32:  # 2^32 = 1 (mod D'): the carry adds one
                     s = s - (1 << 32) + 1
             else:
                 s = d0
         else:
             assert 64 - z <= 3 * k and k <= 30
-            s = bits(h, z, k)
+            s = field(h, z, k)
             if z + k < 64:
-                s += bits(h, z + k, min(64 - z - k, k))
+                s += field(h, z + k, min(64 - z - k, k))
             if z + 2 * k < 64:
-                s += bits(h, z + 2 * k, 64 - z - 2 * k)
+                s += field(h, z + 2 * k, 64 - z - 2 * k)
         assert s < 1 << 32  # the kernel sums in 32-bit registers
         r = s % dp
     if t:
-        return (r << t) | bits(h, a, t)
+        return (r << t) | field(h, a, t)
     return r
 
 
@@ -94,6 +106,17 @@ def test_digit_sum_child_index_equals_the_remainder(leaf, mm, unit):
     hs = [int(x) for x in rng.integers(0, 2**64, 100_000, dtype=np.uint64)] + edge_hashes()
     for h in hs:
         assert child_index(h, mm, a) == (h % mm) >> a, (leaf, mm, h)
+
+
+@pytest.mark.parametrize("leaf,mm,unit", list(full_lower_nodes()))
+def test_the_index_read_before_the_last_xor_shift(leaf, mm, unit):
+    """The kernel reads the digits of h = y ^ (y >> 31) from y directly."""
+    a = ctz(unit)
+    rng = np.random.default_rng(7100 + mm)
+    ys = [int(x) for x in rng.integers(0, 2**64, 100_000, dtype=np.uint64)] + edge_hashes()
+    for y in ys:
+        h = y ^ (y >> 31)
+        assert child_index(y, mm, a, field=hbits_from_pre) == (h % mm) >> a, (leaf, mm, y)
 
 
 @pytest.mark.parametrize("leaf,mm,unit", list(full_lower_nodes()))
