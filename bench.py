@@ -52,14 +52,14 @@ OPS_PER_EVAL = 2 + 8 + 6 + 5 + 3 + 2
 # DRAM bytes the search kernel moves per key (lo word and rotation bit read
 # once per bucket, plus the keys of nodes given to other blocks), from
 # dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_search
-# on 3,000,000 keys of rot_l16 (a multi-wave launch): 28,251,136 B.  The
+# on 3,000,000 keys of rot_l16 (a multi-wave launch): 28,173,568 B.  The
 # traffic of a launch grows with its key count.
-SEARCH_DRAM_BYTES_PER_KEY = 28_251_136 / 3_000_000
+SEARCH_DRAM_BYTES_PER_KEY = 28_173_568 / 3_000_000
 # Pipe utilisation of k_search over the elapsed cycles of the same capture
 # (sm__pipe_fmaheavy_cycles_active, sm__pipe_alu_cycles_active,
 # smsp__issue_active; .avg.pct_of_peak_sustained_elapsed).
-SEARCH_NCU_PIPES = {"fmaheavy_busy_of_elapsed": 0.643, "alu_busy_of_elapsed": 0.791,
-                    "issue_busy_of_elapsed": 0.681, "instructions_per_eval": 31.6,
+SEARCH_NCU_PIPES = {"fmaheavy_busy_of_elapsed": 0.701, "alu_busy_of_elapsed": 0.749,
+                    "issue_busy_of_elapsed": 0.686, "instructions_per_eval": 29.1,
                     "capture": "ncu, k_search on 3e6 keys of rot_l16 (multi-wave), current kernel"}
 LEAF_NAMES = {0: "brute force", 1: "rotation fitting", 2: "ShockHash"}
 
