@@ -400,7 +400,7 @@ constexpr uint32_t kStealReady = 1u << 31;
 constexpr uint32_t kHelpMarker = 0xFFFFFFFEu;  // a steal item inviting a block to a shared search
 
 // Quotient-indexed counter increments of the full lower nodes of the
-// compiled leaf sizes (see DivShift): for leaf size l, fanouts f1, f2 and
+// compiled leaf sizes (see DivNone, QIdx): for leaf size l, fanouts f1, f2 and
 // nodes L1 = f1 l, L2 = f2 L1, a table of L1 >> ctz(l) entries (lower-1
 // nodes, unit l) and one of L2 >> ctz(L1) entries (lower-2 nodes, unit L1).
 __host__ __device__ constexpr uint32_t ctz_ce(uint32_t x) { return (x & 1u) ? 0u : 1u + ctz_ce(x >> 1); }
@@ -434,7 +434,7 @@ struct BlockState {
     unsigned long long lut64[16];  // child -> counter increment (last child: 0)
     uint32_t lut32[16];
     // full lower nodes of a compiled leaf size, unit U = 2^a b: the increment
-    // by p >> a instead of by the child p / U = (p >> a) / b (see DivShift)
+    // by p >> a instead of by the child p / U = (p >> a) / b (see DivNone)
     unsigned long long lutq64[kLutQ];
     uint32_t lutq32[kLutQ];
     InstDesc desc;  // the serving search's current request (read at L2 by load_desc_shared)
@@ -460,18 +460,15 @@ __host__ __device__ constexpr bool counter_fits32(uint32_t m, uint32_t w, uint32
     return ((uint64_t)m << (w * (np - 2))) < (1ull << 32);
 }
 
-template <uint32_t U>
-struct DivCT {
-    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return p / U; }
+// The reduction's result to the index of the counter increment.  For the
+// full lower nodes of the compiled leaf sizes the reduction (QIdx) already
+// yields p >> a for a unit U = 2^a b, the index into S.lutq: the child is
+// p / U = (p >> a) / b (floor of a floor), so that table holds the increment
+// of child q / b at index q, and no division is left in the search loop.
+struct DivNone {
+    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return p; }
 };
-// Position p of a full lower node to the index of its increment in S.lutq:
-// p >> a for a unit U = 2^a b.  The child is p / U = (p >> a) / b (floor of
-// a floor), so the table holds the increment of child q / b at index q, and
-// no division by b is left in the search loop.
-template <uint32_t A>
-struct DivShift {
-    __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return p >> A; }
-};
+// Runtime units: the child p / U by a multiply-high (unit_magic).
 struct DivRT {
     uint32_t magic;
     __device__ __forceinline__ uint32_t operator()(uint32_t p) const { return div_unit(p, magic); }
@@ -1370,7 +1367,7 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             if (m == L1) {
                 const C1 *lut = n1 ? (const C1 *)(S.lutq32 + lutq_off(LEAF, 1)) : (const C1 *)(S.lutq64 + lutq_off(LEAF, 1));
                 const QIdx<L1, a1> mod{};  // the table index p >> a1 straight from the hash
-                const DivShift<0> dv{};
+                const DivNone dv{};
                 x = d.spt == 4 ? search_lower<4, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share)
                   : d.spt == 2 ? search_lower<2, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share)
                                : search_lower<1, C1>(xs, m, mod, dv, lut, (C1)expected, mx, d.max_value, limit, S, share);
@@ -1378,7 +1375,7 @@ __device__ __forceinline__ void split_node(const InstDesc &d, const Shape &sh, u
             } else if (m == L2) {
                 const C2 *lut = n2 ? (const C2 *)(S.lutq32 + lutq_off(LEAF, 2)) : (const C2 *)(S.lutq64 + lutq_off(LEAF, 2));
                 const QIdx<L2, a2> mod{};
-                const DivShift<0> dv{};
+                const DivNone dv{};
                 x = d.spt == 4 ? search_lower<4, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share)
                   : d.spt == 2 ? search_lower<2, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share)
                                : search_lower<1, C2>(xs, m, mod, dv, lut, (C2)expected, mx, d.max_value, limit, S, share);
@@ -1682,7 +1679,7 @@ __device__ __forceinline__ void help_node(const InstDesc &d, HelpRec *rec, uint3
         using C1 = typename std::conditional<n1, uint32_t, unsigned long long>::type;
         using C2 = typename std::conditional<n2, uint32_t, unsigned long long>::type;
         const uint64_t *xs = A.tlo;
-        const DivShift<0> dv1{}, dv2{};
+        const DivNone dv1{}, dv2{};
         if (d.tree == MPHF_TREE_RECSPLIT && m == L1) {
             const C1 *lut = n1 ? (const C1 *)(S.lutq32 + lutq_off(LEAF, 1)) : (const C1 *)(S.lutq64 + lutq_off(LEAF, 1));
             const QIdx<L1, ctz_ce(LEAF)> mod{};
