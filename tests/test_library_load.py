@@ -112,12 +112,12 @@ def test_flipped_bits_in_the_unary_parts_are_refused(lib, orc, bij, tree):
     pos = o.bit_pos.astype(np.int64)
     nodes = np.diff(o.node_off.astype(np.int64))
     for b in (0, 1, o.nb // 2, o.nb - 1):
-        verdict = [_rc(lib, _flip(blob, head_bits + int(p))) for p in range(pos[b], pos[b + 1])]
-        assert set(verdict) <= {M.OK, M.EINVAL}
-        first_refused = verdict.index(M.EINVAL)
-        assert all(v == M.OK for v in verdict[:first_refused])
-        assert all(v == M.EINVAL for v in verdict[first_refused:])
-        assert len(verdict) - first_refused >= nodes[b]
+        codes = [_rc(lib, _flip(blob, head_bits + int(p))) for p in range(pos[b], pos[b + 1])]
+        assert set(codes) <= {M.OK, M.EINVAL}
+        first_refused = codes.index(M.EINVAL)
+        assert all(v == M.OK for v in codes[:first_refused])
+        assert all(v == M.EINVAL for v in codes[first_refused:])
+        assert len(codes) - first_refused >= nodes[b]
 
 
 def test_flipped_bits_in_the_elias_fano_high_vectors_are_refused(lib, orc):
