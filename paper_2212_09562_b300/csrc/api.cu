@@ -64,6 +64,34 @@ int device_mod_tables(int dev, uint32_t **c, uint64_t **M) {
 }
 
 // Per-device copies of the per-size tables; live until the process exits.
+// level_salt(L) for L < kSaltLevels on one device, kept: the query walk reads
+// a fanout-2 level's salt instead of computing its remix.
+static int device_salts(int dev, const uint64_t **out) {
+    static std::mutex mu;
+    static std::map<int, uint64_t *> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) {
+        *out = it->second;
+        return MPHF_OK;
+    }
+    uint64_t h[kSaltLevels];
+    for (uint32_t L = 0; L < kSaltLevels; L++) h[L] = level_salt(L);
+    uint64_t *d = nullptr;
+    if (cudaMalloc(&d, sizeof(h)) != cudaSuccess) {
+        cudaGetLastError();
+        return MPHF_ENOMEM;
+    }
+    if (cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d);
+        return MPHF_ECUDA;
+    }
+    cache[dev] = d;
+    *out = d;
+    return MPHF_OK;
+}
+
 int device_tables(int dev, uint32_t leaf, uint32_t bij, uint32_t tree, DevTables *out) {
     static std::mutex mu;
     static std::map<uint64_t, DevTables> cache;
@@ -86,6 +114,7 @@ int device_tables(int dev, uint32_t leaf, uint32_t bij, uint32_t tree, DevTables
              cudaMemcpy(d.left, t.left, sizeof(t.left), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = MPHF_ECUDA;
     if (rc == MPHF_OK) rc = device_mod_tables(dev, &d.mod_c, &d.mod_M);
+    if (rc == MPHF_OK) rc = device_salts(dev, &d.salts);
     if (rc != MPHF_OK) {  // nothing is cached: free what this call allocated
         cudaGetLastError();
         cudaFree(d.tau);
@@ -708,6 +737,7 @@ static QueryView view_of(const mphf_t *h) {
     q.left_tab = h->tabs.left;
     q.mod_c = h->tabs.mod_c;
     q.mod_M = h->tabs.mod_M;
+    q.salts = h->tabs.salts;
     const Shape shp = make_shape(I.leaf_size, I.tree_shape);
     q.lower1 = shp.lower1;
     q.lower2 = shp.lower2;

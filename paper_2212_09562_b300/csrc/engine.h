@@ -195,6 +195,7 @@ void launch_shard_offsets(const uint64_t *in, uint64_t count, uint64_t base, uin
 void launch_shard_bits(const uint64_t *in, uint64_t bits, uint64_t at, uint64_t *out, cudaStream_t st);
 
 // Query side.
+constexpr uint32_t kSaltLevels = 64;  // salt levels kept in a table (a walk uses at most 16)
 struct QueryView {
     const uint64_t *gr;
     const uint64_t *ef_low[2], *ef_high[2];
@@ -206,6 +207,7 @@ struct QueryView {
     const uint16_t *left_tab;   // left part per fanout-2 node size
     const uint32_t *mod_c;      // exact remainder constants per node size
     const uint64_t *mod_M;
+    const uint64_t *salts;      // level_salt(L) for L < kSaltLevels
     uint64_t nb;
     uint32_t leaf, bij, key_bytes, tree;
     uint32_t magic_leaf, magic_l1;  // ceil(2^32 / l), ceil(2^32 / lower-1 size)

@@ -19,6 +19,7 @@ struct DevTables {
     uint16_t *left = nullptr;
     uint32_t *mod_c = nullptr;
     uint64_t *mod_M = nullptr;
+    const uint64_t *salts = nullptr;  // level_salt(L) for L < kSaltLevels (per device)
 };
 
 // Device memory from the caller's allocator hooks, else stream-ordered

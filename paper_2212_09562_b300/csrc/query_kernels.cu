@@ -142,7 +142,9 @@ __global__ void k_query(QueryView q, const void *keys, uint64_t n, uint64_t *out
             fpos += t;
             idx += 1;
             if (m > lower2) {  // fanout 2: salt 3 + depth
-                const uint32_t pos = mod(mix64(lo + level_salt(3 + depth) + x));
+                const uint32_t L = 3 + depth;  // its salt from the table (a remix otherwise)
+                const uint64_t salt = L < kSaltLevels ? q.salts[L] : level_salt(L);
+                const uint32_t pos = mod(mix64(lo + salt + x));
                 const uint32_t left = q.left_tab[m];
                 if (pos < left) {
                     m = left;
